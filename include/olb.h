@@ -1,0 +1,171 @@
+/*
+ * olb.h -- C ABI of the GB300 (sm_103a) off-lattice Boltzmann library.
+ *
+ * The library advances the two-dimensional thermal lattice Boltzmann model
+ * for van der Waals fluids of Busuioc, Ambrus, Biciusca and Sofonea
+ * (arXiv:1702.01690) by whole TVD RK-3 steps on one GPU.  Each stage
+ * evaluates, at every node, for the 25 populations f_kappa on the
+ * Gauss-Hermite Q = 5 velocity set (Sec. 2.2, Table trots)
+ *
+ *   L[f] = -p . grad f  (WENO-5 fluxes, Sec. 3.2)
+ *          -F . (grad_p f)  (Eq. derf; force F of Eq. F_def from the 49-point
+ *                            stencils of Sec. 3.3)
+ *          -(f - f^eq)/tau  (Eqs. evolution, feq)
+ *
+ * and combines the stages as in Eq. rk3.  Sides normal to x are periodic or
+ * diffuse-reflection walls (Sec. 3.4.2); y is periodic.
+ *
+ * Conventions
+ *  - Every call returns an int status: OLB_OK (0) or a negative OLB_ERR_*.
+ *    No call throws or aborts; olb_status_string() names a status.
+ *  - Host arrays are caller-owned and only read or written during the call.
+ *    Device arrays are caller-owned device pointers on the context's device;
+ *    the library reads or writes them in stream order on the context's
+ *    stream and keeps no reference after the call returns.
+ *  - Fields are FP64 arrays of nx*ny values in row-major [ny][nx] order: the
+ *    value of node (i, j), 0-based, at x = (i + 1/2) ds, y = (j + 1/2) ds
+ *    (Sec. 3.4), is element j*nx + i.
+ *  - Populations are exchanged as FP64 arrays [25][ny][nx]; population
+ *    kappa = 5*k1 + k2 has velocity (R[k1], R[k2]) with R the roots of He_5
+ *    in ascending order (Table trots).
+ *  - A context owns all device memory it uses and runs all its work on one
+ *    CUDA stream (the one given to olb_create, or the legacy default stream
+ *    for NULL).  A context is not thread-safe; distinct contexts are
+ *    independent.
+ */
+#ifndef OLB_H
+#define OLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    OLB_OK = 0,
+    OLB_ERR_ARG = -1,      /* invalid argument (NULL pointer, bad size or enum) */
+    OLB_ERR_CFL = -2,      /* p_max dt / ds >= 1 (Sec. 4.1) or dt > 2.5 tau */
+    OLB_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+    OLB_ERR_DIVERGED = -4, /* a moment became non-finite, n <= 0, b n >= 1 or T <= 0 */
+    OLB_ERR_TIMEOUT = -5,  /* reserved: a bounded device wait ran out */
+    OLB_ERR_STATE = -6,    /* call out of order (e.g. olb_step before init) */
+    OLB_ERR_NOMEM = -7     /* device allocation failed */
+};
+
+/* Boundary kinds of the sides normal to x (side_x) and y (side_y). */
+enum {
+    OLB_SIDE_PERIODIC = 0, /* wrap modulo the grid size */
+    OLB_SIDE_DIFFUSE = 1   /* diffuse-reflection walls at x = 0 and x = nx ds
+                              (Sec. 3.4.2); only valid for side_x */
+};
+
+/* Arithmetic of the populations. */
+enum {
+    OLB_FP64 = 0,       /* everything in FP64 */
+    OLB_FP32_KAHAN = 1  /* populations, fluxes and stencils in FP32; the
+                           25-velocity moment sums Kahan-compensated; T and
+                           Delta p recovered in FP64 */
+};
+
+/* Non-linear WENO weights. */
+enum {
+    OLB_WENO_JS = 0     /* Jiang-Shu weights of Eq. weno5_omega, Table tab:weno */
+};
+
+/* Problem statement (Sec. 2, Sec. 3).  Walls: index 0 is the wall at x = 0,
+ * index 1 the wall at x = nx ds. */
+typedef struct olb_params {
+    int nx, ny;         /* nodes along x and y, >= 1 (>= 3 along x with walls) */
+    double ds;          /* lattice spacing delta s > 0 (Sec. 2.1) */
+    double dt;          /* time step delta t > 0 (Sec. 3.1) */
+    double tau;         /* relaxation time tau > 0, constant (Eq. evolution) */
+    double a, b;        /* van der Waals p^w = n T / (1 - b n) - a n^2;
+                           a = 9/8, b = 1/3 is Eq. vdw; a = b = 0 is the ideal gas */
+    double sigma;       /* surface-tension parameter of Eq. F_def, >= 0 */
+    double Tw[2];       /* wall temperatures T_w > 0 (used with OLB_SIDE_DIFFUSE) */
+    double uw[2];       /* tangential (y) wall velocities u_w */
+    int side_x;         /* OLB_SIDE_PERIODIC or OLB_SIDE_DIFFUSE */
+    int side_y;         /* OLB_SIDE_PERIODIC */
+    int precision;      /* OLB_FP64 or OLB_FP32_KAHAN */
+    int weno_mode;      /* OLB_WENO_JS */
+} olb_params;
+
+typedef struct olb_ctx olb_ctx;
+
+/* Allocator hook.  alloc(bytes, stream, user) returns device memory on the
+ * current device or NULL; release(ptr, bytes, stream, user) frees it.  The
+ * hook is process-wide and applies to contexts created after the call;
+ * passing NULL for both restores cudaMalloc / cudaFree.  Returns OLB_ERR_ARG
+ * if exactly one of the two is NULL.  Not part of the paper: it lets a host
+ * framework (e.g. a caching allocator) own the device memory. */
+typedef void *(*olb_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*olb_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+int olb_set_allocator(olb_alloc_fn alloc, olb_free_fn release, void *user);
+
+/* Validate *p and create a context on the current CUDA device, using
+ * `stream` (a cudaStream_t, or NULL for the legacy default stream) for all
+ * its work.  Device memory (3 population buffers of 25 nx ny values and the
+ * stage fields) is allocated here and nothing is launched.  Rejects
+ * nx, ny < 1, nx < 3 with walls, ds, dt, tau <= 0, sigma < 0, b < 0,
+ * Tw <= 0 with walls, unknown enums (OLB_ERR_ARG) and
+ * p_max dt / ds >= 1 or dt > 2.5 tau (OLB_ERR_CFL; CFL rule of Sec. 4.1,
+ * p_max = sqrt(5 + sqrt 10)).  On success *out receives the context. */
+int olb_create(const olb_params *p, void *stream, olb_ctx **out);
+
+/* Release the context and its device memory (synchronises its stream).
+ * NULL is accepted. */
+void olb_destroy(olb_ctx *ctx);
+
+/* Set f = f^eq(n, u, T) at every node (Eq. feq) from host fields [ny][nx]
+ * and reset the status word.  Rejects non-finite values, n <= 0,
+ * b n >= 1 and T <= 0 with OLB_ERR_ARG before touching the device.
+ * Returns after the device work is complete. */
+int olb_init_fields(olb_ctx *ctx, const double *n, const double *ux,
+                    const double *uy, const double *T);
+
+/* As olb_init_fields with device pointers (FP64, [ny][nx]), enqueued on the
+ * context's stream without synchronisation; the values are not validated
+ * on the host (olb_step's status check sees invalid ones). */
+int olb_init_fields_device(olb_ctx *ctx, const double *n, const double *ux,
+                           const double *uy, const double *T);
+
+/* Advance nsteps >= 0 full RK-3 steps (Eq. rk3), then synchronise and
+ * return OLB_ERR_DIVERGED if any stage met a non-finite moment, n <= 0,
+ * b n >= 1 or T <= 0 (the populations then hold the diverged state),
+ * else OLB_OK. */
+int olb_step(olb_ctx *ctx, int nsteps);
+
+/* As olb_step but only enqueues the work on the context's stream; the
+ * status is read by olb_get_status. */
+int olb_step_async(olb_ctx *ctx, int nsteps);
+
+/* Synchronise the context's stream and return the status word accumulated
+ * since the last init (OLB_OK or OLB_ERR_DIVERGED). */
+int olb_get_status(olb_ctx *ctx);
+
+/* Moments n, u_x, u_y, T of the current populations (Sec. 2.2; T from the
+ * trace of Eq. sigmaq_def) into host arrays [ny][nx].  Any argument may be
+ * NULL to skip it.  Returns after the copies are complete. */
+int olb_moments(olb_ctx *ctx, double *n, double *ux, double *uy, double *T);
+
+/* As olb_moments into device arrays (FP64, [ny][nx]), enqueued on the
+ * context's stream without synchronisation. */
+int olb_moments_device(olb_ctx *ctx, double *n, double *ux, double *uy,
+                       double *T);
+
+/* Copy the populations to / from a host array [25][ny][nx] in FP64 (FP32
+ * contexts round on set).  Used for checkpoint / resume and parity checks.
+ * Both return after the copy is complete. */
+int olb_get_populations(olb_ctx *ctx, double *f);
+int olb_set_populations(olb_ctx *ctx, const double *f);
+
+/* Human-readable name of a status code (static string). */
+const char *olb_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OLB_H */

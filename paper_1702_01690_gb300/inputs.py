@@ -1,0 +1,150 @@
+"""Seeded synthetic initial conditions and run parameters.
+
+This module is shared by the CUDA path, the tests and the benchmark.  It
+holds no arithmetic of the method itself: it only builds initial fields
+(n, u_x, u_y, T) on the node positions x = (i + 1/2) ds, y = (j + 1/2) ds and
+the parameter sets of the workloads.  The paper uses no external dataset;
+every workload is synthetic with the shapes and value distributions of its
+experiments:
+
+  shear wave      u_y = u0 sin(2 pi x), uniform n, T        (Sec. 6.1)
+  planar walls    n = 1 + 0.01 U(-1, 1) per node, T = 1,     (Sec. 7 noise
+                  diffuse walls at x = 0, 1                  recipe, Sec. 4 walls)
+  Laplace drop    tanh drop of radius R, vapour outside      (Sec. 5)
+  phase separation between cold plates                      (Sec. 7)
+
+Random draws use numpy's PCG64 with seed 1702016900 + k, k the workload
+number below, so every run of every leg sees the same values.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, asdict
+
+import numpy as np
+
+SEED_BASE = 1702016900
+P_MAX = math.sqrt(5.0 + math.sqrt(10.0))  # largest Gauss-Hermite Q=5 root
+
+# Coexisting vapour / liquid densities of the reduced van der Waals fluid
+# (a = 9/8, b = 1/3) from the Maxwell equal-area construction; the tests
+# check these constants against the oracle's Maxwell solver.
+MAXWELL = {
+    0.7: (0.1280223017, 2.1404425485),
+    0.8: (0.2396669218, 1.9327058286),
+    0.9: (0.4257416377, 1.6572702120),
+}
+
+
+@dataclass
+class RunParams:
+    nx: int
+    ny: int
+    ds: float
+    dt: float
+    tau: float
+    a: float = 9.0 / 8.0
+    b: float = 1.0 / 3.0
+    sigma: float = 1e-4
+    Tw: tuple = (1.0, 1.0)
+    uw: tuple = (0.0, 0.0)
+    side_x: int = 0     # 0 periodic, 1 diffuse walls
+    side_y: int = 0
+    steps: int = 1
+    name: str = ""
+
+    def as_dict(self):
+        return asdict(self)
+
+    @property
+    def cfl(self) -> float:
+        return P_MAX * self.dt / self.ds
+
+
+def node_x(nx: int, ds: float) -> np.ndarray:
+    return (np.arange(nx) + 0.5) * ds
+
+
+def node_y(ny: int, ds: float) -> np.ndarray:
+    return (np.arange(ny) + 0.5) * ds
+
+
+def shear_wave(nx: int, ny: int, ds: float, n0=1.0, T0=1.1, u0=1e-3, V=0.0):
+    """Uniform n, T; u_y = u0 sin(2 pi x); u_x = V."""
+    x = node_x(nx, ds)
+    n = np.full((ny, nx), float(n0))
+    T = np.full((ny, nx), float(T0))
+    ux = np.full((ny, nx), float(V))
+    uy = np.tile(u0 * np.sin(2.0 * math.pi * x), (ny, 1))
+    return n, ux, uy, T
+
+
+def longitudinal_wave(nx: int, ny: int, ds: float, n0=1.0, T0=1.1, u0=1e-3):
+    x = node_x(nx, ds)
+    n = np.full((ny, nx), float(n0))
+    T = np.full((ny, nx), float(T0))
+    ux = np.tile(u0 * np.sin(2.0 * math.pi * x), (ny, 1))
+    uy = np.zeros((ny, nx))
+    return n, ux, uy, T
+
+
+def noisy_rest(nx: int, ny: int, seed: int, n0=1.0, amp=0.01, T0=1.0):
+    """n = n0 + amp U(-1, 1) per node, u = 0, uniform T (Sec. 7 recipe)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = n0 + amp * rng.uniform(-1.0, 1.0, size=(ny, nx))
+    z = np.zeros((ny, nx))
+    return n, z.copy(), z.copy(), np.full((ny, nx), float(T0))
+
+
+def laplace_drop(nx: int, ny: int, ds: float, R: float, T: float,
+                 width: float = 0.02, centre=(0.5, 0.5)):
+    """Liquid drop of radius R in vapour: n = n_g + (n_l - n_g)/2 (1 - tanh((r - R)/width))."""
+    ng, nl = MAXWELL[round(T, 6)]
+    x = node_x(nx, ds)
+    y = node_y(ny, ds)
+    X, Y = np.meshgrid(x, y)
+    r = np.sqrt((X - centre[0]) ** 2 + (Y - centre[1]) ** 2)
+    n = ng + 0.5 * (nl - ng) * (1.0 - np.tanh((r - R) / width))
+    z = np.zeros((ny, nx))
+    return n, z.copy(), z.copy(), np.full((ny, nx), float(T))
+
+
+# ---------------------------------------------------------------- workloads
+
+def shear_64x4() -> tuple:
+    """Shear-wave decay, 64 x 4 periodic, unit box: n0 = 1, T0 = 1.1,
+    u_y = 1e-3 sin(2 pi x), tau = 0.01, dt = 0.002, 200 RK-3 steps."""
+    p = RunParams(nx=64, ny=4, ds=1.0 / 64, dt=0.002, tau=0.01, steps=200,
+                  name="shear-wave 64x4 periodic")
+    return p, shear_wave(64, 4, p.ds, 1.0, 1.1, 1e-3)
+
+
+def planar_walls(nx: int = 1024, ny: int = 8, steps: int = 20000) -> tuple:
+    """Planar liquid-vapour set-up between diffuse walls at x = 0, 1 (periodic
+    y): T_w = 0.9, n = 1 + 0.01 U(-1,1), T0 = 1, tau = 0.005,
+    dt = 5e-5 * 1024 / nx (CFL 0.146 at nx = 1024), sigma = 1e-4."""
+    ds = 1.0 / nx
+    p = RunParams(nx=nx, ny=ny, ds=ds, dt=5e-5 * 1024.0 / nx, tau=0.005,
+                  Tw=(0.9, 0.9), side_x=1, steps=steps,
+                  name=f"planar interface {nx}x{ny} diffuse walls")
+    return p, noisy_rest(nx, ny, SEED_BASE + 1, 1.0, 0.01, 1.0)
+
+
+def laplace(n: int = 2048, R: float = 0.2, steps: int = 5000) -> tuple:
+    """Laplace drop on an n x n periodic grid, T = 0.9, tanh width 0.02,
+    dt = 2.5e-5 * 2048 / n (CFL 0.146), tau = 5e-3, sigma = 1e-4."""
+    ds = 1.0 / n
+    p = RunParams(nx=n, ny=n, ds=ds, dt=2.5e-5 * 2048.0 / n, tau=5e-3,
+                  steps=steps, name=f"Laplace drop {n}^2 R={R}")
+    return p, laplace_drop(n, n, ds, R, 0.9)
+
+
+def phase_separation(n: int = 4096, Tw: float = 0.7, steps: int = 10000) -> tuple:
+    """Phase separation between cold plates (Sec. 7 set-up): n x n, diffuse
+    walls at x = 0, 1, periodic y, T_w = 0.7, n = 1 + 0.01 U(-1,1), T0 = 1,
+    dt = 1e-5 * 4096 / n (CFL 0.117), tau = 5e-3, sigma = 1e-4."""
+    ds = 1.0 / n
+    p = RunParams(nx=n, ny=n, ds=ds, dt=1e-5 * 4096.0 / n, tau=5e-3,
+                  Tw=(Tw, Tw), side_x=1, steps=steps,
+                  name=f"phase separation {n}^2 Tw={Tw}")
+    return p, noisy_rest(n, n, SEED_BASE + 5, 1.0, 0.01, 1.0)
