@@ -161,6 +161,15 @@ int olb_moments_device(olb_ctx *ctx, double *n, double *ux, double *uy,
 int olb_get_populations(olb_ctx *ctx, double *f);
 int olb_set_populations(olb_ctx *ctx, const double *f);
 
+/* Per-kernel timing (not part of the paper; the tracing hook of the
+ * library).  Runs nsteps RK-3 steps on the context's stream as individual
+ * launches, each bracketed by CUDA events, synchronises, and writes the
+ * mean device time in milliseconds of one launch of each kernel kind to
+ * ms[0] (moments + wall densities) and ms[1] (fused stage), and the number
+ * of launches of each kind to launches[0], launches[1] (either may be NULL).
+ * The populations advance exactly as with olb_step. */
+int olb_profile(olb_ctx *ctx, int nsteps, double *ms, int *launches);
+
 /* Human-readable name of a status code (static string). */
 const char *olb_status_string(int status);
 

@@ -1,0 +1,565 @@
+// olb_api.cu -- the C ABI declared in include/olb.h: parameter validation,
+// device memory, velocity-space tables, CUDA-graph replay of RK-3 steps.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/olb.h"
+#include "olb_internal.cuh"
+
+using namespace olb;
+
+// ---------------------------------------------------------------- tables
+
+namespace olb {
+
+// Probabilists' Hermite polynomial He_l(x) (orthogonal under the weight
+// exp(-x^2/2)/sqrt(2 pi), Eq. eweight).
+static double he(int l, double x)
+{
+    double a = 1.0, b = x;
+    if (l == 0) return a;
+    for (int k = 1; k < l; ++k) {
+        const double c = x * b - k * a;
+        a = b;
+        b = c;
+    }
+    return b;
+}
+
+void host_tables(HostTables *t)
+{
+    // Table trots: roots of He_5 and W_q = 5!/He_6(R_q)^2 in closed form.
+    const double r10 = std::sqrt(10.0);
+    const double big = std::sqrt(5.0 + r10), small = std::sqrt(5.0 - r10);
+    const double R[NQ] = {-big, -small, 0.0, small, big};
+    const double W[NQ] = {(7.0 - 2.0 * r10) / 60.0, (7.0 + 2.0 * r10) / 60.0, 8.0 / 15.0,
+                          (7.0 + 2.0 * r10) / 60.0, (7.0 - 2.0 * r10) / 60.0};
+    for (int k = 0; k < NQ; ++k) {
+        t->R[k] = R[k];
+        t->W[k] = W[k];
+        for (int l = 0; l < NQ; ++l) t->wHe[k][l] = W[k] * he(l, R[k]);
+    }
+    // Eq. derf: (d_p f)_k = -w_k sum_{l<N} He_{l+1}(p_k)/l! sum_k' f_k' He_l(p_k')
+    //         = sum_k' D[k][k'] f_k'
+    const double fact[4] = {1.0, 1.0, 2.0, 6.0};
+    for (int k = 0; k < NQ; ++k)
+        for (int kp = 0; kp < NQ; ++kp) {
+            double s = 0.0;
+            for (int l = 0; l < 4; ++l) s += he(l + 1, R[k]) * he(l, R[kp]) / fact[l];
+            t->D[k][kp] = -W[k] * s;
+        }
+}
+
+// g_k(u, T) of Eq. g_alpha (N = 4, m = 1).
+double host_g(const HostTables &t, int k, double u, double T)
+{
+    const double th = T - 1.0;
+    const double c[5] = {1.0, u, 0.5 * (u * u + th), u * u * u / 6.0 + 0.5 * th * u,
+                         u * u * u * u / 24.0 + 0.25 * th * u * u + 0.125 * th * th};
+    double s = 0.0;
+    for (int l = 0; l < 5; ++l) s += t.wHe[k][l] * c[l];
+    return s;
+}
+
+template <typename real>
+void fill_tab(Tab<real> *tab, const HostTables &h, const double Tw[2], const double uw[2])
+{
+    for (int k = 0; k < NQ; ++k) {
+        tab->R[k] = (real)h.R[k];
+        tab->R2[k] = (real)(h.R[k] * h.R[k]);
+        for (int q = 0; q < NQ; ++q) {
+            tab->D[k][q] = (real)h.D[k][q];
+            tab->wHe[k][q] = (real)h.wHe[k][q];
+        }
+    }
+    for (int s = 0; s < 2; ++s) {
+        double den = 0.0;
+        for (int k1 = 0; k1 < NQ; ++k1)
+            for (int k2 = 0; k2 < NQ; ++k2) {
+                const double gg = host_g(h, k1, 0.0, Tw[s]) * host_g(h, k2, uw[s], Tw[s]);
+                tab->geqw[s][NQ * k1 + k2] = (real)gg;
+                // incoming: p_x > 0 at the wall x = 0, p_x < 0 at x = nx ds
+                const bool incoming = s == 0 ? (k1 > 2) : (k1 < 2);
+                if (incoming) den += gg * h.R[k1];
+            }
+        tab->inv_den[s] = (real)(den != 0.0 ? 1.0 / den : 0.0);
+    }
+}
+template void fill_tab<double>(Tab<double> *, const HostTables &, const double *, const double *);
+template void fill_tab<float>(Tab<float> *, const HostTables &, const double *, const double *);
+
+}  // namespace olb
+
+// ---------------------------------------------------------------- allocator
+
+static olb_alloc_fn g_alloc = nullptr;
+static olb_free_fn g_free = nullptr;
+static void *g_alloc_user = nullptr;
+
+extern "C" int olb_set_allocator(olb_alloc_fn alloc, olb_free_fn release, void *user)
+{
+    if ((alloc == nullptr) != (release == nullptr)) return OLB_ERR_ARG;
+    g_alloc = alloc;
+    g_free = release;
+    g_alloc_user = user;
+    return OLB_OK;
+}
+
+// ---------------------------------------------------------------- context
+
+constexpr int GRAPH_STEPS = 16;  // RK-3 steps per replay of the long graph
+
+struct olb_ctx {
+    olb_params p;
+    int device;
+    cudaStream_t stream;
+    Geo geo;
+    Tab<double> tab64;
+    Tab<float> tab32;
+    size_t elt;                 // bytes per population value
+    void *f[3];                 // f^n, f^(1), f^(2)
+    void *fld, *nw;
+    int *status;
+    double *stage4;             // FP64 [4][ny][nx] staging for host transfers
+    struct Alloc {
+        void *ptr;
+        size_t bytes;
+    } allocs[8];
+    int nallocs;
+    olb_alloc_fn afn;
+    olb_free_fn ffn;
+    void *auser;
+    cudaStream_t cap;
+    cudaGraphExec_t exec1, execG;
+    bool initialized;
+};
+
+static void *ctx_alloc(olb_ctx *c, size_t bytes)
+{
+    void *p = nullptr;
+    if (c->afn) {
+        p = c->afn(bytes, (void *)c->stream, c->auser);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocs[c->nallocs++] = {p, bytes};
+    return p;
+}
+
+static void ctx_free_all(olb_ctx *c)
+{
+    for (int k = 0; k < c->nallocs; ++k) {
+        if (c->ffn)
+            c->ffn(c->allocs[k].ptr, c->allocs[k].bytes, (void *)c->stream, c->auser);
+        else
+            cudaFree(c->allocs[k].ptr);
+    }
+    c->nallocs = 0;
+}
+
+static bool is_fp64(const olb_ctx *c) { return c->p.precision == OLB_FP64; }
+
+// One RK-3 step (Eq. rk3) as 3 x (moments, stage) launches:
+//   f1 = f + dt L[f];  f2 = 3/4 f + 1/4 f1 + 1/4 dt L[f1];
+//   f  = 1/3 f + 2/3 f2 + 2/3 dt L[f2]  (written in place: f is read only at
+//   the node being written).
+template <typename real>
+static cudaError_t enqueue_step(olb_ctx *c, cudaStream_t s)
+{
+    real *f0 = (real *)c->f[0], *f1 = (real *)c->f[1], *f2 = (real *)c->f[2];
+    real *fld = (real *)c->fld, *nw = (real *)c->nw;
+    const Tab<real> &t = *reinterpret_cast<const Tab<real> *>(is_fp64(c) ? (const void *)&c->tab64
+                                                                        : (const void *)&c->tab32);
+    const double dt = c->p.dt;
+    const real *src[3] = {f0, f1, f2};
+    real *dst[3] = {f1, f2, f0};
+    const StageCoef coef[3] = {{0.0, 1.0, dt}, {0.75, 0.25, 0.25 * dt}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt}};
+    for (int st = 0; st < 3; ++st) {
+        cudaError_t e = launch_moments(src[st], fld, nw, c->status, c->geo, t, s);
+        if (e != cudaSuccess) return e;
+        e = launch_stage(src[st], f0, dst[st], fld, nw, c->geo, t, coef[st], s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t enqueue_steps(olb_ctx *c, int n, cudaStream_t s)
+{
+    for (int k = 0; k < n; ++k) {
+        cudaError_t e = is_fp64(c) ? enqueue_step<double>(c, s) : enqueue_step<float>(c, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t build_graph(olb_ctx *c, int nsteps, cudaGraphExec_t *exec)
+{
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t e2 = enqueue_steps(c, nsteps, c->cap);
+    e = cudaStreamEndCapture(c->cap, &graph);
+    if (e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return e2;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
+static int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return OLB_OK;
+    if (e == cudaErrorMemoryAllocation) return OLB_ERR_NOMEM;
+    return OLB_ERR_CUDA;
+}
+
+extern "C" const char *olb_status_string(int status)
+{
+    switch (status) {
+    case OLB_OK: return "OLB_OK";
+    case OLB_ERR_ARG: return "OLB_ERR_ARG: invalid argument";
+    case OLB_ERR_CFL: return "OLB_ERR_CFL: p_max dt/ds >= 1 or dt > 2.5 tau";
+    case OLB_ERR_CUDA: return "OLB_ERR_CUDA: a CUDA runtime call failed";
+    case OLB_ERR_DIVERGED: return "OLB_ERR_DIVERGED: invalid moment (non-finite, n <= 0, b n >= 1 or T <= 0)";
+    case OLB_ERR_TIMEOUT: return "OLB_ERR_TIMEOUT: a bounded device wait ran out";
+    case OLB_ERR_STATE: return "OLB_ERR_STATE: call out of order";
+    case OLB_ERR_NOMEM: return "OLB_ERR_NOMEM: device allocation failed";
+    default: return "unknown olb status";
+    }
+}
+
+static int validate(const olb_params *p)
+{
+    if (!p) return OLB_ERR_ARG;
+    if (p->nx < 1 || p->ny < 1) return OLB_ERR_ARG;
+    if (p->side_x != OLB_SIDE_PERIODIC && p->side_x != OLB_SIDE_DIFFUSE) return OLB_ERR_ARG;
+    if (p->side_y != OLB_SIDE_PERIODIC) return OLB_ERR_ARG;
+    if (p->side_x == OLB_SIDE_DIFFUSE && p->nx < 3) return OLB_ERR_ARG;
+    if (p->precision != OLB_FP64 && p->precision != OLB_FP32_KAHAN) return OLB_ERR_ARG;
+    if (p->weno_mode != OLB_WENO_JS) return OLB_ERR_ARG;
+    if (!(p->ds > 0.0) || !(p->dt > 0.0) || !(p->tau > 0.0)) return OLB_ERR_ARG;
+    if (!std::isfinite(p->ds) || !std::isfinite(p->dt) || !std::isfinite(p->tau)) return OLB_ERR_ARG;
+    if (!(p->sigma >= 0.0) || !(p->b >= 0.0) || !std::isfinite(p->a) || !std::isfinite(p->sigma) ||
+        !std::isfinite(p->b))
+        return OLB_ERR_ARG;
+    if (p->side_x == OLB_SIDE_DIFFUSE)
+        for (int s = 0; s < 2; ++s)
+            if (!(p->Tw[s] > 0.0) || !std::isfinite(p->Tw[s]) || !std::isfinite(p->uw[s])) return OLB_ERR_ARG;
+    if ((long long)p->nx * p->ny > (1LL << 31) / 32) return OLB_ERR_ARG;
+    const double pmax = std::sqrt(5.0 + std::sqrt(10.0));
+    if (!(pmax * p->dt / p->ds < 1.0)) return OLB_ERR_CFL;
+    if (p->dt > 2.5 * p->tau) return OLB_ERR_CFL;
+    return OLB_OK;
+}
+
+extern "C" int olb_create(const olb_params *p, void *stream, olb_ctx **out)
+{
+    if (!out) return OLB_ERR_ARG;
+    *out = nullptr;
+    int v = validate(p);
+    if (v != OLB_OK) return v;
+    olb_ctx *c = new (std::nothrow) olb_ctx();
+    if (!c) return OLB_ERR_NOMEM;
+    c->p = *p;
+    c->stream = (cudaStream_t)stream;
+    c->afn = g_alloc;
+    c->ffn = g_free;
+    c->auser = g_alloc_user;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return OLB_ERR_CUDA;
+    }
+    Geo &g = c->geo;
+    g.nx = p->nx;
+    g.ny = p->ny;
+    g.pitch = (p->nx + 31) / 32 * 32;
+    g.plane = (long long)g.pitch * g.ny;
+    g.walls = p->side_x == OLB_SIDE_DIFFUSE;
+    g.ds = p->ds;
+    g.inv_ds = 1.0 / p->ds;
+    g.inv_ds3 = 1.0 / (p->ds * p->ds * p->ds);
+    g.dt = p->dt;
+    g.inv_tau = 1.0 / p->tau;
+    g.sigma = p->sigma;
+    g.a = p->a;
+    g.b = p->b;
+    HostTables h;
+    host_tables(&h);
+    fill_tab<double>(&c->tab64, h, p->Tw, p->uw);
+    fill_tab<float>(&c->tab32, h, p->Tw, p->uw);
+    c->elt = is_fp64(c) ? sizeof(double) : sizeof(float);
+    const size_t pop = (size_t)NK * g.plane * c->elt;
+    const size_t N = (size_t)g.nx * g.ny;
+    for (int k = 0; k < 3; ++k) c->f[k] = ctx_alloc(c, pop);
+    c->fld = ctx_alloc(c, (size_t)5 * g.plane * c->elt);
+    c->nw = ctx_alloc(c, (size_t)2 * g.ny * c->elt + 256);
+    c->status = (int *)ctx_alloc(c, 256);
+    c->stage4 = (double *)ctx_alloc(c, 4 * N * sizeof(double));
+    bool ok = c->f[0] && c->f[1] && c->f[2] && c->fld && c->nw && c->status && c->stage4;
+    cudaError_t e = cudaSuccess;
+    if (ok) {
+        // zero everything once so padding lanes never hold garbage
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMemsetAsync(c->f[k], 0, pop, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->fld, 0, (size_t)5 * g.plane * c->elt, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->nw, 0, (size_t)2 * g.ny * c->elt, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+        if (e == cudaSuccess) e = is_fp64(c) ? prepare((double *)nullptr) : prepare((float *)nullptr);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (!ok || e != cudaSuccess) {
+        cudaGetLastError();
+        ctx_free_all(c);
+        delete c;
+        return ok ? cuda_status(e) : OLB_ERR_NOMEM;
+    }
+    *out = c;
+    return OLB_OK;
+}
+
+extern "C" void olb_destroy(olb_ctx *c)
+{
+    if (!c) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->exec1) cudaGraphExecDestroy(c->exec1);
+    if (c->execG) cudaGraphExecDestroy(c->execG);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    ctx_free_all(c);
+    cudaGetLastError();
+    cudaSetDevice(prev);
+    delete c;
+}
+
+// Scoped switch to the context's device.
+struct DeviceGuard {
+    int prev;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
+static int init_from_device(olb_ctx *c, const double *n, const double *ux, const double *uy, const double *T)
+{
+    cudaError_t e = is_fp64(c) ? launch_init((double *)c->f[0], n, ux, uy, T, c->geo, c->tab64, c->stream)
+                               : launch_init((float *)c->f[0], n, ux, uy, T, c->geo, c->tab32, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    c->initialized = true;
+    return OLB_OK;
+}
+
+extern "C" int olb_init_fields(olb_ctx *c, const double *n, const double *ux, const double *uy, const double *T)
+{
+    if (!c || !n || !ux || !uy || !T) return OLB_ERR_ARG;
+    const size_t N = (size_t)c->geo.nx * c->geo.ny;
+    for (size_t q = 0; q < N; ++q) {
+        if (!std::isfinite(n[q]) || !std::isfinite(ux[q]) || !std::isfinite(uy[q]) || !std::isfinite(T[q]))
+            return OLB_ERR_ARG;
+        if (!(n[q] > 0.0) || !(T[q] > 0.0) || !(c->p.b * n[q] < 1.0)) return OLB_ERR_ARG;
+    }
+    DeviceGuard dg(c->device);
+    const double *src[4] = {n, ux, uy, T};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(c->stage4 + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int r = init_from_device(c, c->stage4, c->stage4 + N, c->stage4 + 2 * N, c->stage4 + 3 * N);
+    if (r != OLB_OK) return r;
+    return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+extern "C" int olb_init_fields_device(olb_ctx *c, const double *n, const double *ux, const double *uy,
+                                      const double *T)
+{
+    if (!c || !n || !ux || !uy || !T) return OLB_ERR_ARG;
+    DeviceGuard dg(c->device);
+    return init_from_device(c, n, ux, uy, T);
+}
+
+extern "C" int olb_step_async(olb_ctx *c, int nsteps)
+{
+    if (!c || nsteps < 0) return OLB_ERR_ARG;
+    if (!c->initialized) return OLB_ERR_STATE;
+    if (nsteps == 0) return OLB_OK;
+    DeviceGuard dg(c->device);
+    cudaError_t e = cudaSuccess;
+    if (!c->cap) {
+        e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = build_graph(c, 1, &c->exec1);
+        if (e == cudaSuccess) e = build_graph(c, GRAPH_STEPS, &c->execG);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_status(e);
+        }
+    }
+    int k = 0;
+    for (; k + GRAPH_STEPS <= nsteps && e == cudaSuccess; k += GRAPH_STEPS) e = cudaGraphLaunch(c->execG, c->stream);
+    for (; k < nsteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(c->exec1, c->stream);
+    return cuda_status(e);
+}
+
+extern "C" int olb_get_status(olb_ctx *c)
+{
+    if (!c) return OLB_ERR_ARG;
+    DeviceGuard dg(c->device);
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return h ? OLB_ERR_DIVERGED : OLB_OK;
+}
+
+extern "C" int olb_step(olb_ctx *c, int nsteps)
+{
+    int r = olb_step_async(c, nsteps);
+    if (r != OLB_OK) return r;
+    return olb_get_status(c);
+}
+
+static int moments_device(olb_ctx *c, double *n, double *ux, double *uy, double *T)
+{
+    cudaError_t e = is_fp64(c) ? launch_moments_out((const double *)c->f[0], n, ux, uy, T, c->geo, c->tab64, c->stream)
+                               : launch_moments_out((const float *)c->f[0], n, ux, uy, T, c->geo, c->tab32, c->stream);
+    return cuda_status(e);
+}
+
+extern "C" int olb_moments_device(olb_ctx *c, double *n, double *ux, double *uy, double *T)
+{
+    if (!c) return OLB_ERR_ARG;
+    if (!c->initialized) return OLB_ERR_STATE;
+    DeviceGuard dg(c->device);
+    return moments_device(c, n, ux, uy, T);
+}
+
+extern "C" int olb_moments(olb_ctx *c, double *n, double *ux, double *uy, double *T)
+{
+    if (!c) return OLB_ERR_ARG;
+    if (!c->initialized) return OLB_ERR_STATE;
+    DeviceGuard dg(c->device);
+    const size_t N = (size_t)c->geo.nx * c->geo.ny;
+    double *dev[4] = {c->stage4, c->stage4 + N, c->stage4 + 2 * N, c->stage4 + 3 * N};
+    double *host[4] = {n, ux, uy, T};
+    int r = moments_device(c, host[0] ? dev[0] : nullptr, host[1] ? dev[1] : nullptr,
+                           host[2] ? dev[2] : nullptr, host[3] ? dev[3] : nullptr);
+    if (r != OLB_OK) return r;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        if (host[k]) e = cudaMemcpyAsync(host[k], dev[k], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_status(e);
+}
+
+extern "C" int olb_get_populations(olb_ctx *c, double *f)
+{
+    if (!c || !f) return OLB_ERR_ARG;
+    if (!c->initialized) return OLB_ERR_STATE;
+    DeviceGuard dg(c->device);
+    const Geo &g = c->geo;
+    cudaError_t e;
+    if (is_fp64(c)) {
+        e = cudaMemcpy2DAsync(f, (size_t)g.nx * sizeof(double), c->f[0], (size_t)g.pitch * sizeof(double),
+                              (size_t)g.nx * sizeof(double), (size_t)NK * g.ny, cudaMemcpyDeviceToHost, c->stream);
+    } else {
+        const size_t bytes = (size_t)NK * g.nx * g.ny * sizeof(double);
+        double *tmp = nullptr;
+        e = cudaMallocAsync((void **)&tmp, bytes, c->stream);
+        if (e == cudaSuccess) e = launch_to_f64((const float *)c->f[0], tmp, g, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f, tmp, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (tmp) cudaFreeAsync(tmp, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_status(e);
+}
+
+extern "C" int olb_set_populations(olb_ctx *c, const double *f)
+{
+    if (!c || !f) return OLB_ERR_ARG;
+    DeviceGuard dg(c->device);
+    const Geo &g = c->geo;
+    cudaError_t e;
+    if (is_fp64(c)) {
+        e = cudaMemcpy2DAsync(c->f[0], (size_t)g.pitch * sizeof(double), f, (size_t)g.nx * sizeof(double),
+                              (size_t)g.nx * sizeof(double), (size_t)NK * g.ny, cudaMemcpyHostToDevice, c->stream);
+    } else {
+        const size_t bytes = (size_t)NK * g.nx * g.ny * sizeof(double);
+        double *tmp = nullptr;
+        e = cudaMallocAsync((void **)&tmp, bytes, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, f, bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = launch_from_f64((float *)c->f[0], tmp, g, c->stream);
+        if (tmp) cudaFreeAsync(tmp, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) c->initialized = true;
+    return cuda_status(e);
+}
+
+template <typename real>
+static int profile_impl(olb_ctx *c, int nsteps, double *ms, int *launches)
+{
+    real *f0 = (real *)c->f[0], *f1 = (real *)c->f[1], *f2 = (real *)c->f[2];
+    real *fld = (real *)c->fld, *nw = (real *)c->nw;
+    const Tab<real> &t = *reinterpret_cast<const Tab<real> *>(is_fp64(c) ? (const void *)&c->tab64
+                                                                        : (const void *)&c->tab32);
+    const double dt = c->p.dt;
+    const real *src[3] = {f0, f1, f2};
+    real *dst[3] = {f1, f2, f0};
+    const StageCoef coef[3] = {{0.0, 1.0, dt}, {0.75, 0.25, 0.25 * dt}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt}};
+    const int nev = 6 * nsteps;
+    cudaEvent_t *ev = new cudaEvent_t[2 * nev];
+    int made = 0;
+    cudaError_t e = cudaSuccess;
+    for (; made < 2 * nev && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+    int q = 0;
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s)
+        for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+            e = cudaEventRecord(ev[2 * q], c->stream);
+            if (e == cudaSuccess) e = launch_moments(src[st], fld, nw, c->status, c->geo, t, c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * q + 1], c->stream);
+            ++q;
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * q], c->stream);
+            if (e == cudaSuccess) e = launch_stage(src[st], f0, dst[st], fld, nw, c->geo, t, coef[st], c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * q + 1], c->stream);
+            ++q;
+        }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    double acc[2] = {0.0, 0.0};
+    for (int k = 0; k < q && e == cudaSuccess; ++k) {
+        float m = 0.f;
+        e = cudaEventElapsedTime(&m, ev[2 * k], ev[2 * k + 1]);
+        acc[k & 1] += m;
+    }
+    for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    delete[] ev;
+    if (e != cudaSuccess) return cuda_status(e);
+    const int per = 3 * nsteps;
+    if (ms) {
+        ms[0] = per ? acc[0] / per : 0.0;
+        ms[1] = per ? acc[1] / per : 0.0;
+    }
+    if (launches) {
+        launches[0] = per;
+        launches[1] = per;
+    }
+    return OLB_OK;
+}
+
+extern "C" int olb_profile(olb_ctx *c, int nsteps, double *ms, int *launches)
+{
+    if (!c || nsteps < 1) return OLB_ERR_ARG;
+    if (!c->initialized) return OLB_ERR_STATE;
+    DeviceGuard dg(c->device);
+    return is_fp64(c) ? profile_impl<double>(c, nsteps, ms, launches) : profile_impl<float>(c, nsteps, ms, launches);
+}

@@ -1,0 +1,75 @@
+// olb_internal.cuh -- types shared by the library's translation units.
+//
+// Device data layout (all arrays owned by the context):
+//   populations  real f[25][ny][pitch]   kappa = 5*k1 + k2 (x-major velocity
+//                index), pitch = nx rounded up to 32 elements so every row
+//                starts on a 128/256-byte boundary
+//   stage fields real fld[5][ny][pitch]  n, u_x, u_y, T, Delta p of the stage
+//                input (written by the moments kernel, read by the stage
+//                kernel with a 3-node halo)
+//   wall density real nw[2][ny]          n_w of Eq. nw per wall and row
+//   status       int                     bit 0: invalid moment seen
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace olb {
+
+constexpr int NQ = 5;   // Gauss-Hermite points per axis (Table trots)
+constexpr int NK = 25;  // velocities
+
+// Geometry and physical parameters, passed by value to every kernel.
+struct Geo {
+    int nx, ny, pitch;
+    int walls;           // 1: diffuse walls at x = 0 and x = nx ds
+    long long plane;     // pitch * ny
+    double ds, inv_ds, inv_ds3, dt, inv_tau, sigma, a, b;
+};
+
+// Velocity-space tables (Sec. 2.2, 2.3), in the population precision.
+template <typename real>
+struct Tab {
+    real R[NQ];          // roots of He_5, ascending
+    real R2[NQ];         // R^2
+    real D[NQ][NQ];      // (d_p f)_k = sum_k' D[k][k'] f_k'   (Eq. derf)
+    real wHe[NQ][NQ];    // w_k He_l(p_k), l = 0..4            (Eq. g_alpha)
+    real geqw[2][NK];    // g_{k1}(0, Tw) g_{k2}(uw, Tw) per wall
+    real inv_den[2];     // 1 / sum_incoming g g p per wall    (Eq. nw)
+};
+
+// Host-side tables in FP64 (computed once from the closed forms).
+struct HostTables {
+    double R[NQ], W[NQ], D[NQ][NQ], wHe[NQ][NQ];
+};
+void host_tables(HostTables *t);
+double host_g(const HostTables &t, int k, double u, double T);
+
+template <typename real>
+void fill_tab(Tab<real> *tab, const HostTables &h, const double Tw[2], const double uw[2]);
+
+// RK-3 stage coefficients: out = ca f^n + cb f_s + cc L[f_s] (Eq. rk3).
+struct StageCoef {
+    double ca, cb, cc;
+};
+
+// Launchers, one set per precision (olb_fp64.cu, olb_fp32.cu).  Output
+// pointers of moments_out may be NULL to skip a field.
+#define OLB_DECLARE_LAUNCHERS(real)                                                                    \
+    cudaError_t prepare(real *);                                                                       \
+    cudaError_t launch_moments(const real *f, real *fld, real *nw, int *status, const Geo &g,          \
+                               const Tab<real> &t, cudaStream_t s);                                     \
+    cudaError_t launch_stage(const real *fs, const real *fn, real *out, const real *fld,                \
+                             const real *nw, const Geo &g, const Tab<real> &t, StageCoef c,             \
+                             cudaStream_t s);                                                           \
+    cudaError_t launch_init(real *f, const double *n, const double *ux, const double *uy,              \
+                            const double *T, const Geo &g, const Tab<real> &t, cudaStream_t s);         \
+    cudaError_t launch_moments_out(const real *f, double *n, double *ux, double *uy, double *T,        \
+                                   const Geo &g, const Tab<real> &t, cudaStream_t s);                   \
+    cudaError_t launch_to_f64(const real *f, double *dst, const Geo &g, cudaStream_t s);               \
+    cudaError_t launch_from_f64(real *f, const double *src, const Geo &g, cudaStream_t s);
+
+OLB_DECLARE_LAUNCHERS(double)
+OLB_DECLARE_LAUNCHERS(float)
+
+}  // namespace olb

@@ -1,0 +1,235 @@
+"""ctypes binding of libolb.so (include/olb.h).  Argument marshalling only:
+every step of the method runs in the library's CUDA kernels.
+
+Importing this module loads ``_build/libolb.so`` and raises ImportError if it
+is missing (build it with ``python -m paper_1702_01690_gb300.build``); there
+is no CPU fallback.  PyTorch supplies the CUDA stream of a context and, via
+the allocator hook, its device memory (torch's caching allocator).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+if not os.path.exists(LIB):
+    raise ImportError(f"libolb.so not built ({LIB}); run python -m paper_1702_01690_gb300.build")
+
+_lib = ctypes.CDLL(LIB)
+
+OK = 0
+ERR_ARG, ERR_CFL, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE, ERR_NOMEM = -1, -2, -3, -4, -5, -6, -7
+SIDE_PERIODIC, SIDE_DIFFUSE = 0, 1
+FP64, FP32_KAHAN = 0, 1
+WENO_JS = 0
+
+SYMBOLS = ("olb_set_allocator", "olb_create", "olb_destroy", "olb_init_fields",
+           "olb_init_fields_device", "olb_step", "olb_step_async", "olb_get_status",
+           "olb_moments", "olb_moments_device", "olb_get_populations",
+           "olb_set_populations", "olb_status_string", "olb_profile")
+
+
+class Params(ctypes.Structure):
+    """Mirror of olb_params."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("ds", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("Tw", ctypes.c_double * 2), ("uw", ctypes.c_double * 2),
+                ("side_x", ctypes.c_int), ("side_y", ctypes.c_int),
+                ("precision", ctypes.c_int), ("weno_mode", ctypes.c_int)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib.olb_set_allocator.argtypes = [ALLOC_FN, FREE_FN, _VP]
+_lib.olb_set_allocator.restype = ctypes.c_int
+_lib.olb_create.argtypes = [ctypes.POINTER(Params), _VP, ctypes.POINTER(_VP)]
+_lib.olb_create.restype = ctypes.c_int
+_lib.olb_destroy.argtypes = [_VP]
+_lib.olb_destroy.restype = None
+for _n in ("olb_init_fields", "olb_init_fields_device", "olb_moments", "olb_moments_device"):
+    getattr(_lib, _n).argtypes = [_VP, _VP, _VP, _VP, _VP]
+    getattr(_lib, _n).restype = ctypes.c_int
+for _n in ("olb_step", "olb_step_async"):
+    getattr(_lib, _n).argtypes = [_VP, ctypes.c_int]
+    getattr(_lib, _n).restype = ctypes.c_int
+_lib.olb_get_status.argtypes = [_VP]
+_lib.olb_get_status.restype = ctypes.c_int
+for _n in ("olb_get_populations", "olb_set_populations"):
+    getattr(_lib, _n).argtypes = [_VP, _VP]
+    getattr(_lib, _n).restype = ctypes.c_int
+_lib.olb_profile.argtypes = [_VP, ctypes.c_int, _VP, _VP]
+_lib.olb_profile.restype = ctypes.c_int
+_lib.olb_status_string.argtypes = [ctypes.c_int]
+_lib.olb_status_string.restype = ctypes.c_char_p
+
+
+class OlbError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+
+
+def status_string(code: int) -> str:
+    return _lib.olb_status_string(int(code)).decode()
+
+
+def _check(code: int, what: str) -> int:
+    if code != OK:
+        raise OlbError(code, what)
+    return code
+
+
+def library():
+    return _lib
+
+
+# ------------------------------------------------------------ torch allocator hook
+_hook_refs = None
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Route the library's device allocations through torch's caching
+    allocator (applies to contexts created afterwards)."""
+    global _hook_refs
+    if not enable:
+        _check(_lib.olb_set_allocator(ALLOC_FN(0), FREE_FN(0), None), "olb_set_allocator")
+        _hook_refs = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    refs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(_lib.olb_set_allocator(refs[0], refs[1], None), "olb_set_allocator")
+    _hook_refs = refs
+
+
+# ------------------------------------------------------------ marshalling helpers
+
+def _host_ptr(a):
+    assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_VP)
+
+
+def _dev_ptr(t):
+    assert t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()
+    return _VP(t.data_ptr())
+
+
+def params_from(run, precision: int = FP64) -> Params:
+    """Params from any object with the fields of inputs.RunParams."""
+    p = Params()
+    p.nx, p.ny = int(run.nx), int(run.ny)
+    p.ds, p.dt, p.tau = float(run.ds), float(run.dt), float(run.tau)
+    p.a, p.b, p.sigma = float(run.a), float(run.b), float(run.sigma)
+    p.Tw[0], p.Tw[1] = float(run.Tw[0]), float(run.Tw[1])
+    p.uw[0], p.uw[1] = float(run.uw[0]), float(run.uw[1])
+    p.side_x, p.side_y = int(run.side_x), int(run.side_y)
+    p.precision = int(precision)
+    p.weno_mode = WENO_JS
+    return p
+
+
+class Context:
+    """One olb_ctx.  Fields are (ny, nx) float64 arrays: numpy arrays go
+    through the host entry points, CUDA tensors through the device ones."""
+
+    def __init__(self, params: Params, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        self.nx, self.ny = params.nx, params.ny
+        self.params = params
+        h = _VP()
+        _check(_lib.olb_create(ctypes.byref(params), _VP(stream.cuda_stream), ctypes.byref(h)),
+               "olb_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.olb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init_fields(self, n, ux, uy, T):
+        arrs = (n, ux, uy, T)
+        if isinstance(n, np.ndarray):
+            arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self.ny, self.nx) for a in arrs]
+            _check(_lib.olb_init_fields(self._h, *[_host_ptr(a) for a in arrs]), "olb_init_fields")
+        else:
+            _check(_lib.olb_init_fields_device(self._h, *[_dev_ptr(a) for a in arrs]),
+                   "olb_init_fields_device")
+
+    def step(self, nsteps: int = 1) -> int:
+        return _check(_lib.olb_step(self._h, int(nsteps)), "olb_step")
+
+    def step_async(self, nsteps: int = 1) -> None:
+        _check(_lib.olb_step_async(self._h, int(nsteps)), "olb_step_async")
+
+    def status(self) -> int:
+        return _lib.olb_get_status(self._h)
+
+    def moments(self):
+        out = [np.zeros((self.ny, self.nx)) for _ in range(4)]
+        _check(_lib.olb_moments(self._h, *[_host_ptr(a) for a in out]), "olb_moments")
+        return tuple(out)
+
+    def moments_device(self, out=None):
+        import torch
+        if out is None:
+            out = [torch.empty((self.ny, self.nx), dtype=torch.float64, device="cuda") for _ in range(4)]
+        _check(_lib.olb_moments_device(self._h, *[_dev_ptr(a) for a in out]), "olb_moments_device")
+        return tuple(out)
+
+    def profile(self, nsteps: int):
+        """Mean device ms per launch of (moments, stage) and launch counts."""
+        ms = np.zeros(2)
+        cnt = np.zeros(2, dtype=np.int32)
+        _check(_lib.olb_profile(self._h, int(nsteps), ms.ctypes.data_as(_VP), cnt.ctypes.data_as(_VP)),
+               "olb_profile")
+        return {"moments_ms": float(ms[0]), "stage_ms": float(ms[1]),
+                "moments_launches": int(cnt[0]), "stage_launches": int(cnt[1])}
+
+    def get_populations(self) -> np.ndarray:
+        out = np.zeros((25, self.ny, self.nx))
+        _check(_lib.olb_get_populations(self._h, _host_ptr(out)), "olb_get_populations")
+        return out
+
+    def set_populations(self, f) -> None:
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(25, self.ny, self.nx)
+        _check(_lib.olb_set_populations(self._h, _host_ptr(f)), "olb_set_populations")
+
+
+def create(run, precision: int = FP64, stream=None) -> Context:
+    return Context(params_from(run, precision), stream)

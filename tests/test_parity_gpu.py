@@ -1,0 +1,252 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 contract: n, u, T within 1e-11 of the oracle relative to each field's
+magnitude after 200 steps of the shear-wave workload; populations within
+1e-12 after single steps.  FP32 + Kahan: within 1e-5 on n and T; u, which
+is a small difference of O(1) populations, is reported against the same
+bound relative to |u| + 1e-3 |n| (see the design notes)."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import field_rel, make_oracle, moments_rel
+from paper_1702_01690_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def olb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_01690_gb300 import build
+    build.build()
+    from paper_1702_01690_gb300 import olb as mod
+    return mod
+
+
+def run_pair(olb, p, fields, steps, precision=0):
+    ctx = olb.create(p, precision)
+    ctx.init_fields(*fields)
+    o = make_oracle(p, fields)
+    if steps:
+        assert ctx.step(steps) == 0
+        o.step(steps)
+    return ctx, o
+
+
+def noisy(p, seed=5, amp=0.01, T0=1.0, uamp=0.0):
+    n, ux, uy, T = inputs.noisy_rest(p.nx, p.ny, seed, 1.0, amp, T0)
+    if uamp:
+        rng = np.random.default_rng(seed + 1)
+        ux = uamp * rng.uniform(-1, 1, n.shape)
+        uy = uamp * rng.uniform(-1, 1, n.shape)
+    return n, ux, uy, T
+
+
+# ------------------------------------------------------------------ basics
+
+def test_init_is_equilibrium(olb):
+    p, fl = inputs.shear_64x4()
+    ctx, o = run_pair(olb, p, fl, 0)
+    assert field_rel(ctx.get_populations(), o.get_populations()) < 1e-14
+    m = ctx.moments()
+    for a, b in zip(m, fl):
+        assert np.max(np.abs(a - b)) < 1e-14
+
+
+@pytest.mark.parametrize("side_x", [0, 1])
+def test_one_step_populations(olb, side_x):
+    p, _ = inputs.planar_walls(nx=40, ny=8)
+    p.side_x = side_x
+    ctx, o = run_pair(olb, p, noisy(p, uamp=0.02), 1)
+    assert field_rel(ctx.get_populations(), o.get_populations()) < 1e-12
+
+
+def test_shear_wave_200_steps_fp64(olb):
+    """Shear-wave workload (64 x 4, 200 RK-3 steps): 1e-11 on n, u, T."""
+    p, fl = inputs.shear_64x4()
+    ctx, o = run_pair(olb, p, fl, p.steps)
+    err = moments_rel(ctx.moments(), o.moments())
+    assert max(err.values()) < FP64_TOL, err
+
+
+@pytest.mark.parametrize("nx,ny,side_x", [(37, 11, 0), (45, 3, 1), (3, 1, 1), (1, 5, 0), (70, 9, 1), (33, 17, 0)])
+def test_ragged_and_tiny_grids(olb, nx, ny, side_x):
+    """Grids that leave ragged tiles, fewer rows than the stencil, and the
+    smallest wall domain (nx = 3)."""
+    p = inputs.RunParams(nx=nx, ny=ny, ds=1.0 / max(nx, 8), dt=0.2 / max(nx, 8) / inputs.P_MAX,
+                         tau=0.01, Tw=(0.85, 0.95), uw=(0.01, -0.02), side_x=side_x)
+    ctx, o = run_pair(olb, p, noisy(p, seed=nx * 31 + ny, amp=0.05, uamp=0.01), 10)
+    err = moments_rel(ctx.moments(), o.moments())
+    assert max(err.values()) < FP64_TOL, err
+    assert field_rel(ctx.get_populations(), o.get_populations()) < FP64_TOL
+
+
+def test_planar_walls_full_grid(olb):
+    """Planar-interface workload at its full size (1024 x 8, diffuse walls,
+    the launch configuration the benchmark times) for 20 steps."""
+    p, fl = inputs.planar_walls()
+    ctx, o = run_pair(olb, p, fl, 20)
+    err = moments_rel(ctx.moments(), o.moments())
+    assert max(err.values()) < FP64_TOL, err
+
+
+def test_graph_replay_matches_single_steps(olb):
+    """16-step graph + 1-step graph replay = 17 single-step calls, bit for bit."""
+    p, _ = inputs.planar_walls(nx=48, ny=8)
+    fl = noisy(p)
+    a = olb.create(p)
+    a.init_fields(*fl)
+    a.step(17)
+    b = olb.create(p)
+    b.init_fields(*fl)
+    for _ in range(17):
+        b.step(1)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+
+
+def test_set_get_populations_roundtrip_and_resume(olb):
+    """Checkpoint / resume: stepping 5 + 5 with a host round trip in between
+    equals 10 continuous steps bit for bit."""
+    p, _ = inputs.planar_walls(nx=40, ny=6)
+    fl = noisy(p)
+    a = olb.create(p)
+    a.init_fields(*fl)
+    a.step(10)
+    b = olb.create(p)
+    b.init_fields(*fl)
+    b.step(5)
+    snap = b.get_populations()
+    c = olb.create(p)
+    c.set_populations(snap)
+    c.step(5)
+    assert np.array_equal(a.get_populations(), c.get_populations())
+
+
+def test_device_entry_points(olb):
+    import torch
+    p, fl = inputs.shear_64x4()
+    ctx = olb.create(p)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in fl]
+    ctx.init_fields(*dev)
+    ctx.step_async(3)
+    assert ctx.status() == 0
+    md = [t.cpu().numpy() for t in ctx.moments_device()]
+    torch.cuda.synchronize()
+    mh = ctx.moments()
+    for a, b in zip(md, mh):
+        assert np.array_equal(a, b)
+    o = make_oracle(p, fl)
+    o.step(3)
+    assert max(moments_rel(mh, o.moments()).values()) < FP64_TOL
+
+
+def test_diverged_state_reported(olb):
+    """A state with negative density is reported as OLB_ERR_DIVERGED by the
+    status word, never as a device fault."""
+    p, fl = inputs.shear_64x4()
+    ctx = olb.create(p)
+    ctx.init_fields(*fl)
+    ctx.set_populations(-np.abs(ctx.get_populations()))
+    rc = olb.library().olb_step(ctx.handle, 1)
+    assert rc == olb.ERR_DIVERGED
+    ctx.init_fields(*fl)  # init clears the status
+    assert ctx.step(1) == 0
+
+
+def test_init_fields_rejects_invalid_values(olb):
+    p, fl = inputs.shear_64x4()
+    ctx = olb.create(p)
+    n, ux, uy, T = [a.copy() for a in fl]
+    n[0, 0] = -1.0
+    with pytest.raises(olb.OlbError):
+        ctx.init_fields(n, ux, uy, T)
+    n[0, 0] = 3.5  # b n >= 1
+    with pytest.raises(olb.OlbError):
+        ctx.init_fields(n, ux, uy, T)
+    with pytest.raises(olb.OlbError):
+        ctx.step(1)  # not initialised
+
+
+# ------------------------------------------------------------------ full-size samples
+
+def crop_window(fields, x0, y0, wx, wy, nx, ny, periodic_x):
+    """Sub-window [x0, x0+wx) x [y0, y0+wy) of (ny, nx) fields with y (and x
+    when periodic) wrapped."""
+    ys = np.arange(y0, y0 + wy) % ny
+    xs = np.arange(x0, x0 + wx)
+    if periodic_x:
+        xs = xs % nx
+    return tuple(np.ascontiguousarray(a[np.ix_(ys, xs)]) for a in fields)
+
+
+def window_check(olb, p, fields, windows, margin=10, steps=1):
+    """One GPU run at full size; the oracle on windows around sample points.
+    A node depends on nodes at most 3 away per stage (WENO stencil and the
+    49-point stencils of pointwise moments), 9 per RK-3 step, so the window
+    interior more than 9*steps from a cut edge is exact."""
+    ctx = olb.create(p)
+    ctx.init_fields(*fields)
+    assert ctx.step(steps) == 0
+    m_gpu = ctx.moments()
+    worst = 0.0
+    for (x0, y0, wx, wy, at_wall) in windows:
+        wp = inputs.RunParams(**{**p.as_dict(), "nx": wx, "ny": wy})
+        if not at_wall:
+            wp.side_x = 0
+        sub = crop_window(fields, x0, y0, wx, wy, p.nx, p.ny, p.side_x == 0)
+        o = make_oracle(wp, sub)
+        o.step(steps)
+        mo = o.moments()
+        inner_y = slice(margin * steps, wy - margin * steps)
+        if at_wall == "left":
+            inner_x = slice(0, wx - margin * steps)
+        elif at_wall == "right":
+            inner_x = slice(margin * steps, wx)
+        else:
+            inner_x = slice(margin * steps, wx - margin * steps)
+        ys = np.arange(y0, y0 + wy) % p.ny
+        xs = np.arange(x0, x0 + wx) % p.nx
+        g = tuple(a[np.ix_(ys, xs)][inner_y, inner_x] for a in m_gpu)
+        r = tuple(a[inner_y, inner_x] for a in mo)
+        worst = max(worst, max(moments_rel(g, r).values()))
+    return worst
+
+
+def test_laplace_2048_sampled_windows(olb):
+    """Laplace-drop workload at full size (2048^2 periodic) after one step,
+    sampled on oracle windows across the drop interface and in the bulk."""
+    p, fl = inputs.laplace(2048, R=0.2, steps=1)
+    wins = [(1024 - 20 + dx, 1024 + 410 - 20 + dy, 40, 40, None) for dx, dy in ((0, 0), (300, -100))]
+    wins += [(2048 - 20, 2048 - 20, 40, 40, None)]  # wraps both axes
+    assert window_check(olb, p, fl, wins) < FP64_TOL
+
+
+def test_phase_separation_4096_sampled_windows(olb):
+    """Cold-plate workload at full size (4096^2, diffuse walls) after one step,
+    sampled on oracle windows at both walls and in the bulk."""
+    p, fl = inputs.phase_separation(4096, steps=1)
+    wins = [(0, 100, 40, 40, "left"), (4096 - 40, 3000, 40, 40, "right"), (2000, 4096 - 20, 40, 40, None)]
+    assert window_check(olb, p, fl, wins) < FP64_TOL
+
+
+# ------------------------------------------------------------------ FP32 + Kahan
+
+def test_fp32_kahan_shear_wave(olb):
+    p, fl = inputs.shear_64x4()
+    ctx, o = run_pair(olb, p, fl, p.steps, precision=olb.FP32_KAHAN)
+    err = moments_rel(ctx.moments(), o.moments())
+    assert err["n"] < 1e-5 and err["T"] < 1e-5, err
+    assert err["u"] < 5e-3, err
+
+
+def test_fp32_kahan_planar_walls(olb):
+    p, fl = inputs.planar_walls(nx=256, ny=8)
+    ctx, o = run_pair(olb, p, fl, 100, precision=olb.FP32_KAHAN)
+    err = moments_rel(ctx.moments(), o.moments())
+    assert err["n"] < 1e-5 and err["T"] < 1e-5, err
