@@ -63,7 +63,7 @@ def load_peaks():
         return {}
 
 
-def workload(name):
+def workload(name, size=None):
     from paper_1702_01690_gb300 import inputs
     if name == "planar":
         p, f = inputs.planar_walls()
@@ -72,11 +72,13 @@ def workload(name):
         p, f = inputs.shear_64x4()
         desc = "shear-wave decay 64x4 periodic, T0=1.1, tau=0.01, dt=0.002"
     elif name == "laplace":
-        p, f = inputs.laplace(2048, R=0.2)
-        desc = "Laplace drop 2048^2 periodic, R=0.2, T=0.9, tau=5e-3, dt=2.5e-5"
+        n = size or 2048
+        p, f = inputs.laplace(n, R=0.2)
+        desc = f"Laplace drop {n}^2 periodic, R=0.2, T=0.9, tau=5e-3, dt={p.dt:g}"
     elif name == "phase":
-        p, f = inputs.phase_separation(4096)
-        desc = "phase separation 4096^2, diffuse walls, Tw=0.7, tau=5e-3, dt=1e-5"
+        n = size or 4096
+        p, f = inputs.phase_separation(n)
+        desc = f"phase separation {n}^2, diffuse walls, Tw=0.7, tau=5e-3, dt={p.dt:g}"
     else:
         raise SystemExit(f"unknown workload {name}")
     return p, f, desc
@@ -169,7 +171,7 @@ def oracle_sample_params(p, fields, max_nodes=1 << 16):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    p, fields, desc = workload(args.workload)
+    p, fields, desc = workload(args.workload, args.size)
     q, sub, what = oracle_sample_params(p, fields)
     # untimed warm-up steps, then K timed whole-grid steps of the sample
     import oracle
@@ -221,7 +223,7 @@ def run_ours(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    p, fields, desc = workload(args.workload)
+    p, fields, desc = workload(args.workload, args.size)
     N = p.nx * p.ny
     olb.use_torch_allocator(True)
     dev_fields = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in fields]
@@ -315,6 +317,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="planar", choices=["planar", "shear", "laplace", "phase"])
+    ap.add_argument("--size", type=int, default=None, help="grid size of the laplace / phase workloads")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
