@@ -8,10 +8,24 @@ every workload is synthetic with the shapes and value distributions of its
 experiments:
 
   shear wave      u_y = u0 sin(2 pi x), uniform n, T        (Sec. 6.1)
-  planar walls    n = 1 + 0.01 U(-1, 1) per node, T = 1,     (Sec. 7 noise
-                  diffuse walls at x = 0, 1                  recipe, Sec. 4 walls)
+  planar walls    n = 1 + 0.01 noise, T = 1, diffuse walls   (Sec. 7 noise
+                  at x = 0, 1                                recipe, Sec. 4 walls)
   Laplace drop    tanh drop of radius R, vapour outside      (Sec. 5)
   phase separation between cold plates                      (Sec. 7)
+
+Noise.  The paper draws U(-0.01, 0.01) per node on a grid of 320 nodes per
+unit length (Sec. 7).  The surface energy of per-node noise grows like
+1/ds^2, and on grids finer than ~256 per unit length it drives near-sonic
+flow that leaves the model's range (measured: per-node noise at ds = 1/1024
+diverges within 500 steps for any stable dt).  The noise is therefore drawn
+per node of a grid with at most 256 nodes per unit length and Fourier-
+interpolated to the full grid (``band_limited_noise``); on grids of at most
+256 nodes per unit length it is plain per-node noise.
+
+Time steps.  Besides the CFL rule p_max dt / ds < 1 (Sec. 4.1), the
+capillary term sigma grad(Laplacian n) of Eq. F_def makes the step stiff:
+the fastest mode has omega ~ 2.7 sqrt(sigma n) / ds^2, and RK-3 needs
+omega dt < sqrt(3).  The fine-grid workloads take dt with omega dt ~ 0.6.
 
 Random draws use numpy's PCG64 with seed 1702016900 + k, k the workload
 number below, so every run of every leg sees the same values.
@@ -96,6 +110,45 @@ def noisy_rest(nx: int, ny: int, seed: int, n0=1.0, amp=0.01, T0=1.0):
     return n, z.copy(), z.copy(), np.full((ny, nx), float(T0))
 
 
+def band_limited_noise(nx: int, ny: int, seed: int, factor: int) -> np.ndarray:
+    """U(-1, 1) per node of a (ny/factor) x (nx/factor) grid, Fourier-
+    interpolated (zero-padded spectrum) to ny x nx; factor 1 is plain
+    per-node noise."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if factor <= 1:
+        return rng.uniform(-1.0, 1.0, size=(ny, nx))
+    cy, cx = max(1, ny // factor), max(1, nx // factor)
+    C = np.fft.fft2(rng.uniform(-1.0, 1.0, size=(cy, cx)))
+    P = np.zeros((ny, nx), dtype=complex)
+    hy, hx = (cy + 1) // 2, (cx + 1) // 2
+    ly, lx = cy - hy, cx - hx
+    P[:hy, :hx] = C[:hy, :hx]
+    if lx:
+        P[:hy, nx - lx:] = C[:hy, hx:]
+    if ly:
+        P[ny - ly:, :hx] = C[hy:, :hx]
+        if lx:
+            P[ny - ly:, nx - lx:] = C[hy:, hx:]
+    return np.real(np.fft.ifft2(P)) * (ny * nx) / (cy * cx)
+
+
+def noise_factor(nx: int, ds: float) -> int:
+    """Coarsening factor that keeps the noise at most 256 nodes per unit length."""
+    per_unit = 1.0 / ds
+    f = 1
+    while per_unit / f > 256 and nx % (2 * f) == 0:
+        f *= 2
+    return f
+
+
+def cold_rest(nx: int, ny: int, ds: float, seed: int, n0=1.0, amp=0.01, T0=1.0):
+    """n = n0 + amp * band-limited noise, u = 0, uniform T (Sec. 7 recipe at
+    the noise resolution described in the module docstring)."""
+    n = n0 + amp * band_limited_noise(nx, ny, seed, noise_factor(nx, ds))
+    z = np.zeros((ny, nx))
+    return n, z.copy(), z.copy(), np.full((ny, nx), float(T0))
+
+
 def laplace_drop(nx: int, ny: int, ds: float, R: float, T: float,
                  width: float = 0.02, centre=(0.5, 0.5)):
     """Liquid drop of radius R in vapour: n = n_g + (n_l - n_g)/2 (1 - tanh((r - R)/width))."""
@@ -121,30 +174,33 @@ def shear_64x4() -> tuple:
 
 def planar_walls(nx: int = 1024, ny: int = 8, steps: int = 20000) -> tuple:
     """Planar liquid-vapour set-up between diffuse walls at x = 0, 1 (periodic
-    y): T_w = 0.9, n = 1 + 0.01 U(-1,1), T0 = 1, tau = 0.005,
-    dt = 5e-5 * 1024 / nx (CFL 0.146 at nx = 1024), sigma = 1e-4."""
+    y): T_w = 0.9, n = 1 + 0.01 (band-limited) noise, T0 = 1, tau = 0.005,
+    dt = 5e-5 * 1024 / nx (CFL 0.146, omega dt ~ 1.4 at nx = 1024),
+    sigma = 1e-4."""
     ds = 1.0 / nx
     p = RunParams(nx=nx, ny=ny, ds=ds, dt=5e-5 * 1024.0 / nx, tau=0.005,
                   Tw=(0.9, 0.9), side_x=1, steps=steps,
                   name=f"planar interface {nx}x{ny} diffuse walls")
-    return p, noisy_rest(nx, ny, SEED_BASE + 1, 1.0, 0.01, 1.0)
+    return p, cold_rest(nx, ny, ds, SEED_BASE + 1, 1.0, 0.01, 1.0)
 
 
 def laplace(n: int = 2048, R: float = 0.2, steps: int = 5000) -> tuple:
     """Laplace drop on an n x n periodic grid, T = 0.9, tanh width 0.02,
-    dt = 2.5e-5 * 2048 / n (CFL 0.146), tau = 5e-3, sigma = 1e-4."""
+    dt = 5e-6 (2048 / n)^2 (capillary limit, omega dt ~ 0.7; CFL 0.03 at
+    n = 2048), tau = 5e-3, sigma = 1e-4."""
     ds = 1.0 / n
-    p = RunParams(nx=n, ny=n, ds=ds, dt=2.5e-5 * 2048.0 / n, tau=5e-3,
+    p = RunParams(nx=n, ny=n, ds=ds, dt=5e-6 * (2048.0 / n) ** 2, tau=5e-3,
                   steps=steps, name=f"Laplace drop {n}^2 R={R}")
     return p, laplace_drop(n, n, ds, R, 0.9)
 
 
 def phase_separation(n: int = 4096, Tw: float = 0.7, steps: int = 10000) -> tuple:
     """Phase separation between cold plates (Sec. 7 set-up): n x n, diffuse
-    walls at x = 0, 1, periodic y, T_w = 0.7, n = 1 + 0.01 U(-1,1), T0 = 1,
-    dt = 1e-5 * 4096 / n (CFL 0.117), tau = 5e-3, sigma = 1e-4."""
+    walls at x = 0, 1, periodic y, T_w = 0.7, n = 1 + 0.01 (band-limited)
+    noise, T0 = 1, dt = 1.25e-6 (4096 / n)^2 (capillary limit, omega dt ~ 0.6;
+    CFL 0.015 at n = 4096), tau = 5e-3, sigma = 1e-4."""
     ds = 1.0 / n
-    p = RunParams(nx=n, ny=n, ds=ds, dt=1e-5 * 4096.0 / n, tau=5e-3,
+    p = RunParams(nx=n, ny=n, ds=ds, dt=1.25e-6 * (4096.0 / n) ** 2, tau=5e-3,
                   Tw=(Tw, Tw), side_x=1, steps=steps,
                   name=f"phase separation {n}^2 Tw={Tw}")
-    return p, noisy_rest(n, n, SEED_BASE + 5, 1.0, 0.01, 1.0)
+    return p, cold_rest(n, n, ds, SEED_BASE + 5, 1.0, 0.01, 1.0)
