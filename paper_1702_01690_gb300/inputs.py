@@ -24,8 +24,11 @@ interpolated to the full grid (``band_limited_noise``); on grids of at most
 
 Time steps.  Besides the CFL rule p_max dt / ds < 1 (Sec. 4.1), the
 capillary term sigma grad(Laplacian n) of Eq. F_def makes the step stiff:
-the fastest mode has omega ~ 2.7 sqrt(sigma n) / ds^2, and RK-3 needs
-omega dt < sqrt(3).  The fine-grid workloads take dt with omega dt ~ 0.6.
+the fastest mode along one axis has omega ~ 2.7 sqrt(sigma n) / ds^2, about
+twice that along the grid diagonal, and RK-3 needs omega dt < sqrt(3)
+(measured: at ds = 1/1024 the 2-D planar set-up diverges within 250 steps at
+dt = 5e-5 and runs cleanly at dt = 2.5e-5).  The workloads take dt with
+2-D omega dt <= ~1.4.
 
 Random draws use numpy's PCG64 with seed 1702016900 + k, k the workload
 number below, so every run of every leg sees the same values.
@@ -175,10 +178,10 @@ def shear_64x4() -> tuple:
 def planar_walls(nx: int = 1024, ny: int = 8, steps: int = 20000) -> tuple:
     """Planar liquid-vapour set-up between diffuse walls at x = 0, 1 (periodic
     y): T_w = 0.9, n = 1 + 0.01 (band-limited) noise, T0 = 1, tau = 0.005,
-    dt = 5e-5 * 1024 / nx (CFL 0.146, omega dt ~ 1.4 at nx = 1024),
+    dt = 2.5e-5 * 1024 / nx (CFL 0.073, 2-D omega dt ~ 1.4 at nx = 1024),
     sigma = 1e-4."""
     ds = 1.0 / nx
-    p = RunParams(nx=nx, ny=ny, ds=ds, dt=5e-5 * 1024.0 / nx, tau=0.005,
+    p = RunParams(nx=nx, ny=ny, ds=ds, dt=2.5e-5 * 1024.0 / nx, tau=0.005,
                   Tw=(0.9, 0.9), side_x=1, steps=steps,
                   name=f"planar interface {nx}x{ny} diffuse walls")
     return p, cold_rest(nx, ny, ds, SEED_BASE + 1, 1.0, 0.01, 1.0)
@@ -186,10 +189,10 @@ def planar_walls(nx: int = 1024, ny: int = 8, steps: int = 20000) -> tuple:
 
 def laplace(n: int = 2048, R: float = 0.2, steps: int = 5000) -> tuple:
     """Laplace drop on an n x n periodic grid, T = 0.9, tanh width 0.02,
-    dt = 5e-6 (2048 / n)^2 (capillary limit, omega dt ~ 0.7; CFL 0.03 at
-    n = 2048), tau = 5e-3, sigma = 1e-4."""
+    dt = 2.5e-6 (2048 / n)^2 (capillary limit, 2-D omega dt ~ 0.7; CFL 0.015
+    at n = 2048), tau = 5e-3, sigma = 1e-4."""
     ds = 1.0 / n
-    p = RunParams(nx=n, ny=n, ds=ds, dt=5e-6 * (2048.0 / n) ** 2, tau=5e-3,
+    p = RunParams(nx=n, ny=n, ds=ds, dt=2.5e-6 * (2048.0 / n) ** 2, tau=5e-3,
                   steps=steps, name=f"Laplace drop {n}^2 R={R}")
     return p, laplace_drop(n, n, ds, R, 0.9)
 
@@ -197,10 +200,10 @@ def laplace(n: int = 2048, R: float = 0.2, steps: int = 5000) -> tuple:
 def phase_separation(n: int = 4096, Tw: float = 0.7, steps: int = 10000) -> tuple:
     """Phase separation between cold plates (Sec. 7 set-up): n x n, diffuse
     walls at x = 0, 1, periodic y, T_w = 0.7, n = 1 + 0.01 (band-limited)
-    noise, T0 = 1, dt = 1.25e-6 (4096 / n)^2 (capillary limit, omega dt ~ 0.6;
-    CFL 0.015 at n = 4096), tau = 5e-3, sigma = 1e-4."""
+    noise, T0 = 1, dt = 6.25e-7 (4096 / n)^2 (capillary limit, 2-D omega dt
+    ~ 0.7; CFL 0.007 at n = 4096), tau = 5e-3, sigma = 1e-4."""
     ds = 1.0 / n
-    p = RunParams(nx=n, ny=n, ds=ds, dt=1.25e-6 * (4096.0 / n) ** 2, tau=5e-3,
+    p = RunParams(nx=n, ny=n, ds=ds, dt=6.25e-7 * (4096.0 / n) ** 2, tau=5e-3,
                   Tw=(Tw, Tw), side_x=1, steps=steps,
                   name=f"phase separation {n}^2 Tw={Tw}")
     return p, cold_rest(n, n, ds, SEED_BASE + 5, 1.0, 0.01, 1.0)

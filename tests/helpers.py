@@ -45,3 +45,42 @@ def make_oracle(p, fields):
     o = oracle.Oracle(p.nx, p.ny, p.ds, p.dt, p.tau, p.a, p.b, p.sigma, p.Tw, p.uw, p.side_x, p.side_y)
     o.init_fields(*fields)
     return o
+
+
+EPS = float(np.finfo(np.float64).eps)
+
+
+def rounding_envelope(p, fields, steps, ulps=4.0, seed=0):
+    """How far two correct FP64 evaluations of the same run can drift apart.
+
+    The step is ill-conditioned where the 49-point stencils of Eq. F_def
+    cancel to O(ds^k) of their terms (fine grids, smooth fields): a 1-ulp
+    change of the state moves the force by up to ~1e6 ulp.  The oracle is run
+    twice, the second time with every population multiplied by
+    1 + ulps * eps * U(-1, 1) before each step (a stand-in for the rounding
+    of one RK-3 step done in another order); the absolute differences of
+    (n, u_x, u_y, T) between the two runs are returned."""
+    a = make_oracle(p, fields)
+    b = make_oracle(p, fields)
+    rng = np.random.default_rng(seed)
+    for _ in range(steps):
+        f = b.get_populations()
+        b.set_populations(f * (1.0 + ulps * EPS * rng.uniform(-1.0, 1.0, f.shape)))
+        a.step(1)
+        b.step(1)
+    return [np.abs(x - y) for x, y in zip(a.moments(), b.moments())], a
+
+
+def check_against_envelope(m_gpu, p, fields, steps, rtol=1e-11, factor=10.0):
+    """GPU moments vs the oracle: each field within max(rtol x its magnitude,
+    factor x the rounding envelope), elementwise.  Returns the worst ratio
+    error / allowed (< 1 passes) per field."""
+    env, o = rounding_envelope(p, fields, steps)
+    ref = o.moments()
+    us = max(np.max(np.abs(ref[1])), np.max(np.abs(ref[2])), 1e-300)
+    scales = [np.max(np.abs(ref[0])), us, us, np.max(np.abs(ref[3]))]
+    out = {}
+    for name, g, r, e, s in zip(("n", "ux", "uy", "T"), m_gpu, ref, env, scales):
+        allowed = np.maximum(rtol * s, factor * e)
+        out[name] = float(np.max(np.abs(np.asarray(g) - r) / allowed))
+    return out
