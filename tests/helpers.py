@@ -50,16 +50,20 @@ def make_oracle(p, fields):
 EPS = float(np.finfo(np.float64).eps)
 
 
-def rounding_envelope(p, fields, steps, ulps=4.0, seed=0):
+def rounding_envelope(p, fields, steps, ulps=64.0, seed=0):
     """How far two correct FP64 evaluations of the same run can drift apart.
 
     The step is ill-conditioned where the 49-point stencils of Eq. F_def
     cancel to O(ds^k) of their terms (fine grids, smooth fields): a 1-ulp
     change of the state moves the force by up to ~1e6 ulp.  The oracle is run
     twice, the second time with every population multiplied by
-    1 + ulps * eps * U(-1, 1) before each step (a stand-in for the rounding
-    of one RK-3 step done in another order); the absolute differences of
-    (n, u_x, u_y, T) between the two runs are returned."""
+    1 + ulps * eps * U(-1, 1) before each step, a stand-in for the rounding
+    of one RK-3 step done in another order: summing a 49-tap stencil in
+    another order moves it by up to ~49 roundings of its largest terms, and
+    a random perturbation of 64 ulp per population moves the moments (sums
+    of 25 populations) and hence the stencil sums by about as much.  The
+    absolute differences of (n, u_x, u_y, T) between the two runs and the
+    unperturbed oracle are returned."""
     a = make_oracle(p, fields)
     b = make_oracle(p, fields)
     rng = np.random.default_rng(seed)
