@@ -39,20 +39,23 @@ sys.path.insert(0, ROOT)
 METRIC = "node-updates/s (25-vel RK3 step) vs plain FP64 at stated error; % of roofline"
 UNIT = "node-updates/s"
 
-# Algorithmic FP64 flops of the fused stage kernel per node and stage
-# (FMA = 2), counted formula by formula (see the design notes):
-#   force stencils 172, equilibrium factors 104, local part of L and RK
-#   partial sums 25 x 30 = 750, WENO-5 faces 40 x 57 = 2280 (20 moving
-#   velocities per axis, one face per node), advection and output 155.
-STAGE_FLOPS_PER_NODE = 172 + 104 + 750 + 2280 + 155
-MOMENTS_FLOPS_PER_NODE = 110
-# Population values moved per node and stage by the fused stage kernel:
-# read f_s (25), read f^n (25, stages 2 and 3), write (25); 200 per RK-3 step.
-STAGE_VALUES_PER_NODE_STEP = 200
+# Algorithmic flops of one stage per node (FMA = 2), counted formula by
+# formula (see the design notes): moments 110, force stencils 172,
+# equilibrium factors 104, local part of L and RK combination 25 x 30 = 750,
+# WENO-5 faces 40 x 57 = 2280 (20 moving velocities per axis, one face per
+# node), advection and output 155.  The FP32 variant adds the Kahan
+# compensation of the four 25-term moment sums (+365).
+STAGE_FLOPS_PER_NODE = 110 + 172 + 104 + 750 + 2280 + 155
+STAGE_FLOPS_PER_NODE_FP32 = STAGE_FLOPS_PER_NODE + 365
+# Population values moved per node and step: stage 1 reads f and writes f1
+# (50), stages 2 and 3 read f^n and f_s and write (75 each): 200 per step.
+VALUES_PER_NODE_STEP = 200
 
-# FP64 peak of a GB300 (TFLOP/s): 1.25 from the recipe's nominal figure.
-# FP32 peak: 152 SMs x 128 lanes x 2 flops x 2.07 GHz.
-PEAK_FP64_TFLOPS = 1.25
+# Peaks from unit counts and the 2.07 GHz maximum SM clock: FP64 2 DFMA per
+# SM per clock (1.20 TFLOP/s measured at 1.97 GHz with an FMA loop),
+# 152 x 2 x 2 x 2.07e9 = 1.26 TFLOP/s; FP32 128 lanes per SM,
+# 152 x 128 x 2 x 2.07e9 = 80.5 TFLOP/s.
+PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
@@ -250,13 +253,13 @@ def run_ours(args, rank, world):
     prof = ctx.profile(max(3, min(args.steps, 50)))
     st_ms = prof["stage_ms"]
     achieved = STAGE_FLOPS_PER_NODE * N / (st_ms * 1e-3) / 1e12
-    roof = {"kernel": "k_stage<double,32,8> (fused force + WENO-5 + BGK + RK-3)",
+    tile = ctx.get_tile()
+    roof = {"kernel": f"k_fused<double,{tile[0]},{tile[1]}> (moments + force + WENO-5 + BGK + RK-3 stage)",
             "bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
-            "peak_source": "FP64 1.25 TFLOP/s nominal GB300 figure of the profiling recipe",
+            "peak_source": "FP64 units x max SM clock (2 DFMA/SM/clk x 152 x 2.07 GHz)",
             "algorithmic_flops_per_launch": STAGE_FLOPS_PER_NODE * N,
-            "stage_ms": st_ms, "moments_ms": prof["moments_ms"],
-            "stage_share": 3 * st_ms / ms_step if ms_step > 0 else None}
+            "stage_ms": st_ms, "stage_share": 3 * st_ms / ms_step if ms_step > 0 else None}
 
     # FP32 + Kahan variant on the same workload
     ctx32 = olb.create(p, olb.FP32_KAHAN, stream)
@@ -264,7 +267,8 @@ def run_ours(args, rank, world):
     total32, _ = time_steps(ctx32, args.steps, args.warmup, flush, stream)
     m32 = ctx32.moments()
     prof32 = ctx32.profile(max(3, min(args.steps, 50)))
-    ach32 = STAGE_FLOPS_PER_NODE * N / (prof32["stage_ms"] * 1e-3) / 1e12
+    ach32 = STAGE_FLOPS_PER_NODE_FP32 * N / (prof32["stage_ms"] * 1e-3) / 1e12
+    tile32 = ctx32.get_tile()
     us = max(np.max(np.abs(m64[1])), np.max(np.abs(m64[2])), 1e-300)
     err32 = {"n": float(np.max(np.abs(m32[0] - m64[0])) / np.max(np.abs(m64[0]))),
              "u": float(max(np.max(np.abs(m32[1] - m64[1])), np.max(np.abs(m32[2] - m64[2]))) / us),
@@ -272,7 +276,7 @@ def run_ours(args, rank, world):
     v32 = world * N * args.steps / (total32 / 1e3)
     fp32 = {"value": v32, "ms_per_step": total32 / args.steps, "speedup_vs_fp64": v32 / value,
             "max_rel_err_vs_fp64_after_steps": err32, "steps_compared": args.warmup + args.steps,
-            "roofline": {"kernel": "k_stage<float,32,8>", "bound": "alu", "achieved": ach32,
+            "roofline": {"kernel": f"k_fused<float,{tile32[0]},{tile32[1]}>", "bound": "alu", "achieved": ach32,
                          "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": ach32 / PEAK_FP32_TFLOPS,
                          "stage_ms": prof32["stage_ms"]}}
     ctx32.close()
@@ -301,7 +305,7 @@ def run_ours(args, rank, world):
                        "l2": "256 MiB buffer written between timed steps",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof, "fp32_kahan": fp32, "e2e": e2e,
-            "gpu_launches": 6 * args.steps, "clocks": clk.summary()}
+            "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, steps, el, cores = oracle_rate(p, fields, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",

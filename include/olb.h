@@ -162,13 +162,19 @@ int olb_get_populations(olb_ctx *ctx, double *f);
 int olb_set_populations(olb_ctx *ctx, const double *f);
 
 /* Per-kernel timing (not part of the paper; the tracing hook of the
- * library).  Runs nsteps RK-3 steps on the context's stream as individual
- * launches, each bracketed by CUDA events, synchronises, and writes the
- * mean device time in milliseconds of one launch of each kernel kind to
- * ms[0] (moments + wall densities) and ms[1] (fused stage), and the number
- * of launches of each kind to launches[0], launches[1] (either may be NULL).
- * The populations advance exactly as with olb_step. */
+ * library).  Runs nsteps >= 1 RK-3 steps on the context's stream as
+ * individual launches of the stage kernel, each bracketed by CUDA events,
+ * synchronises, and writes the mean device time in milliseconds of one
+ * launch to ms[0] and the number of launches to launches[0] (either may be
+ * NULL).  The populations advance exactly as with olb_step. */
 int olb_profile(olb_ctx *ctx, int nsteps, double *ms, int *launches);
+
+/* Tile shape of the stage kernel (nodes per CTA along x and y).  Compiled
+ * shapes: 8x8, 16x8, 32x8, 32x16; olb_create picks one from the grid size.
+ * olb_set_tile returns OLB_ERR_ARG for any other shape; results do not
+ * depend on the shape.  Not part of the paper (a tuning knob). */
+int olb_set_tile(olb_ctx *ctx, int tx, int ty);
+int olb_get_tile(olb_ctx *ctx, int *tx, int *ty);
 
 /* Human-readable name of a status code (static string). */
 const char *olb_status_string(int status);

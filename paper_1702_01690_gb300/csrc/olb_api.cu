@@ -120,8 +120,8 @@ struct olb_ctx {
     Tab<float> tab32;
     size_t elt;                 // bytes per population value
     void *f[3];                 // f^n, f^(1), f^(2)
-    void *fld, *nw;
     int *status;
+    int tx, ty;                 // stage-kernel tile shape
     double *stage4;             // FP64 [4][ny][nx] staging for host transfers
     struct Alloc {
         void *ptr;
@@ -162,25 +162,40 @@ static void ctx_free_all(olb_ctx *c)
 
 static bool is_fp64(const olb_ctx *c) { return c->p.precision == OLB_FP64; }
 
-// One RK-3 step (Eq. rk3) as 3 x (moments, stage) launches:
+// One RK-3 step (Eq. rk3) as 3 launches of the fused stage kernel:
 //   f1 = f + dt L[f];  f2 = 3/4 f + 1/4 f1 + 1/4 dt L[f1];
 //   f  = 1/3 f + 2/3 f2 + 2/3 dt L[f2]  (written in place: f is read only at
 //   the node being written).
+static const double *stage_coef(double dt, int st, StageCoef *c)
+{
+    const StageCoef coef[3] = {{0.0, 1.0, dt}, {0.75, 0.25, 0.25 * dt}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt}};
+    *c = coef[st];
+    return nullptr;
+}
+
+template <typename real>
+static const Tab<real> &ctx_tab(const olb_ctx *c);
+template <>
+const Tab<double> &ctx_tab<double>(const olb_ctx *c) { return c->tab64; }
+template <>
+const Tab<float> &ctx_tab<float>(const olb_ctx *c) { return c->tab32; }
+
+template <typename real>
+static cudaError_t enqueue_stage(olb_ctx *c, int st, cudaStream_t s)
+{
+    real *f0 = (real *)c->f[0], *f1 = (real *)c->f[1], *f2 = (real *)c->f[2];
+    const real *src[3] = {f0, f1, f2};
+    real *dst[3] = {f1, f2, f0};
+    StageCoef coef;
+    stage_coef(c->p.dt, st, &coef);
+    return launch_fused(src[st], f0, dst[st], c->status, c->geo, ctx_tab<real>(c), coef, c->tx, c->ty, s);
+}
+
 template <typename real>
 static cudaError_t enqueue_step(olb_ctx *c, cudaStream_t s)
 {
-    real *f0 = (real *)c->f[0], *f1 = (real *)c->f[1], *f2 = (real *)c->f[2];
-    real *fld = (real *)c->fld, *nw = (real *)c->nw;
-    const Tab<real> &t = *reinterpret_cast<const Tab<real> *>(is_fp64(c) ? (const void *)&c->tab64
-                                                                        : (const void *)&c->tab32);
-    const double dt = c->p.dt;
-    const real *src[3] = {f0, f1, f2};
-    real *dst[3] = {f1, f2, f0};
-    const StageCoef coef[3] = {{0.0, 1.0, dt}, {0.75, 0.25, 0.25 * dt}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt}};
     for (int st = 0; st < 3; ++st) {
-        cudaError_t e = launch_moments(src[st], fld, nw, c->status, c->geo, t, s);
-        if (e != cudaSuccess) return e;
-        e = launch_stage(src[st], f0, dst[st], fld, nw, c->geo, t, coef[st], s);
+        cudaError_t e = enqueue_stage<real>(c, st, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -258,6 +273,29 @@ static int validate(const olb_params *p)
     return OLB_OK;
 }
 
+static cudaError_t prepare_tile(olb_ctx *c)
+{
+    return is_fp64(c) ? prepare_fused((double *)nullptr, c->tx, c->ty) : prepare_fused((float *)nullptr, c->tx, c->ty);
+}
+
+// Default tile: the largest shape that still gives every SM two CTAs, else
+// the smallest shape (most CTAs, for small grids).  FP64 stays at <= 16 x 8
+// nodes so that two CTAs share an SM: the FP64 pipe idles while a lone CTA
+// waits at a barrier.  Shapes are listed by increasing area.
+static void default_tile(olb_ctx *c)
+{
+    const long long two_per_sm = 2 * 152;
+    int best = 0;
+    for (int k = 0; k < NUM_TILES; ++k) {
+        if (is_fp64(c) && TILE_X[k] * TILE_Y[k] > 128) continue;
+        const long long ctas =
+            (long long)((c->geo.nx + TILE_X[k] - 1) / TILE_X[k]) * ((c->geo.ny + TILE_Y[k] - 1) / TILE_Y[k]);
+        if (ctas >= two_per_sm) best = k;
+    }
+    c->tx = TILE_X[best];
+    c->ty = TILE_Y[best];
+}
+
 extern "C" int olb_create(const olb_params *p, void *stream, olb_ctx **out)
 {
     if (!out) return OLB_ERR_ARG;
@@ -298,19 +336,16 @@ extern "C" int olb_create(const olb_params *p, void *stream, olb_ctx **out)
     const size_t pop = (size_t)NK * g.plane * c->elt;
     const size_t N = (size_t)g.nx * g.ny;
     for (int k = 0; k < 3; ++k) c->f[k] = ctx_alloc(c, pop);
-    c->fld = ctx_alloc(c, (size_t)5 * g.plane * c->elt);
-    c->nw = ctx_alloc(c, (size_t)2 * g.ny * c->elt + 256);
     c->status = (int *)ctx_alloc(c, 256);
     c->stage4 = (double *)ctx_alloc(c, 4 * N * sizeof(double));
-    bool ok = c->f[0] && c->f[1] && c->f[2] && c->fld && c->nw && c->status && c->stage4;
+    default_tile(c);
+    bool ok = c->f[0] && c->f[1] && c->f[2] && c->status && c->stage4;
     cudaError_t e = cudaSuccess;
     if (ok) {
         // zero everything once so padding lanes never hold garbage
         for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMemsetAsync(c->f[k], 0, pop, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->fld, 0, (size_t)5 * g.plane * c->elt, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->nw, 0, (size_t)2 * g.ny * c->elt, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
-        if (e == cudaSuccess) e = is_fp64(c) ? prepare((double *)nullptr) : prepare((float *)nullptr);
+        if (e == cudaSuccess) e = prepare_tile(c);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     }
     if (!ok || e != cudaSuccess) {
@@ -338,6 +373,8 @@ extern "C" void olb_destroy(olb_ctx *c)
     cudaSetDevice(prev);
     delete c;
 }
+
+static void drop_graphs(olb_ctx *c);
 
 // Scoped switch to the context's device.
 struct DeviceGuard {
@@ -509,50 +546,30 @@ extern "C" int olb_set_populations(olb_ctx *c, const double *f)
 template <typename real>
 static int profile_impl(olb_ctx *c, int nsteps, double *ms, int *launches)
 {
-    real *f0 = (real *)c->f[0], *f1 = (real *)c->f[1], *f2 = (real *)c->f[2];
-    real *fld = (real *)c->fld, *nw = (real *)c->nw;
-    const Tab<real> &t = *reinterpret_cast<const Tab<real> *>(is_fp64(c) ? (const void *)&c->tab64
-                                                                        : (const void *)&c->tab32);
-    const double dt = c->p.dt;
-    const real *src[3] = {f0, f1, f2};
-    real *dst[3] = {f1, f2, f0};
-    const StageCoef coef[3] = {{0.0, 1.0, dt}, {0.75, 0.25, 0.25 * dt}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt}};
-    const int nev = 6 * nsteps;
+    const int nev = 3 * nsteps;
     cudaEvent_t *ev = new cudaEvent_t[2 * nev];
     int made = 0;
     cudaError_t e = cudaSuccess;
     for (; made < 2 * nev && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
     int q = 0;
     for (int s = 0; s < nsteps && e == cudaSuccess; ++s)
-        for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+        for (int st = 0; st < 3 && e == cudaSuccess; ++st, ++q) {
             e = cudaEventRecord(ev[2 * q], c->stream);
-            if (e == cudaSuccess) e = launch_moments(src[st], fld, nw, c->status, c->geo, t, c->stream);
+            if (e == cudaSuccess) e = enqueue_stage<real>(c, st, c->stream);
             if (e == cudaSuccess) e = cudaEventRecord(ev[2 * q + 1], c->stream);
-            ++q;
-            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * q], c->stream);
-            if (e == cudaSuccess) e = launch_stage(src[st], f0, dst[st], fld, nw, c->geo, t, coef[st], c->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * q + 1], c->stream);
-            ++q;
         }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    double acc[2] = {0.0, 0.0};
+    double acc = 0.0;
     for (int k = 0; k < q && e == cudaSuccess; ++k) {
         float m = 0.f;
         e = cudaEventElapsedTime(&m, ev[2 * k], ev[2 * k + 1]);
-        acc[k & 1] += m;
+        acc += m;
     }
     for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
     delete[] ev;
     if (e != cudaSuccess) return cuda_status(e);
-    const int per = 3 * nsteps;
-    if (ms) {
-        ms[0] = per ? acc[0] / per : 0.0;
-        ms[1] = per ? acc[1] / per : 0.0;
-    }
-    if (launches) {
-        launches[0] = per;
-        launches[1] = per;
-    }
+    if (ms) ms[0] = q ? acc / q : 0.0;
+    if (launches) launches[0] = q;
     return OLB_OK;
 }
 
@@ -562,4 +579,44 @@ extern "C" int olb_profile(olb_ctx *c, int nsteps, double *ms, int *launches)
     if (!c->initialized) return OLB_ERR_STATE;
     DeviceGuard dg(c->device);
     return is_fp64(c) ? profile_impl<double>(c, nsteps, ms, launches) : profile_impl<float>(c, nsteps, ms, launches);
+}
+
+static void drop_graphs(olb_ctx *c)
+{
+    if (c->exec1) cudaGraphExecDestroy(c->exec1);
+    if (c->execG) cudaGraphExecDestroy(c->execG);
+    c->exec1 = c->execG = nullptr;
+    if (c->cap) cudaStreamDestroy(c->cap);
+    c->cap = nullptr;
+}
+
+extern "C" int olb_set_tile(olb_ctx *c, int tx, int ty)
+{
+    if (!c) return OLB_ERR_ARG;
+    int k = 0;
+    while (k < NUM_TILES && !(TILE_X[k] == tx && TILE_Y[k] == ty)) ++k;
+    if (k == NUM_TILES) return OLB_ERR_ARG;
+    DeviceGuard dg(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int otx = c->tx, oty = c->ty;
+    c->tx = tx;
+    c->ty = ty;
+    e = prepare_tile(c);
+    if (e != cudaSuccess) {
+        c->tx = otx;
+        c->ty = oty;
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    drop_graphs(c);
+    return OLB_OK;
+}
+
+extern "C" int olb_get_tile(olb_ctx *c, int *tx, int *ty)
+{
+    if (!c || !tx || !ty) return OLB_ERR_ARG;
+    *tx = c->tx;
+    *ty = c->ty;
+    return OLB_OK;
 }

@@ -1,6 +1,8 @@
-// olb_fp64.cu -- FP64 instantiation of the stage kernels (32 x 8 node tiles).
-#include "olb_kernels.cuh"
+// olb_fp64.cu -- FP64 instances of the stage kernel (all tile shapes) and of
+// the initialisation / output kernels.
+#include "olb_fused.cuh"
 
 namespace olb {
-OLB_DEFINE_LAUNCHERS(double, 32, 8)
+OLB_DEFINE_FUSED(double)
+OLB_DEFINE_AUX_LAUNCHERS(double)
 }  // namespace olb

@@ -1,0 +1,351 @@
+// olb_fused.cuh -- one RK-3 stage of the off-lattice Boltzmann model in a
+// single kernel per stage (templated on precision and tile shape).
+//
+// One CTA owns a TX x TY tile of nodes and stages the populations of the
+// tile plus a 3-node halo on every side in shared memory:
+//   1. load f_s for the (TX+8) x (TY+6) region (x offset -4 keeps rows
+//      16-byte aligned for vector loads; y and periodic x wrap);
+//   2. moments n, u, T, Delta p at every fluid node of the region (Sec. 2.2,
+//      Eq. vdw), with the even reflection of Delta p and n at walls
+//      (Sec. 3.4.3);
+//   3. walls (Sec. 3.4.2): extrapolated ghosts for the outgoing velocities,
+//      the WENO flux of those velocities at the wall face, summed over the
+//      10 velocities with warp shuffles into n_w (Eq. nw), and f^eq_w ghosts
+//      for the incoming velocities;
+//   4. force F = grad(Delta p)/n + sigma grad(Laplacian n) at the tile nodes
+//      from the 49-point stencils (Eqs. F_def, stencil_grad, stencil_glap);
+//   5. for each velocity: every x and y face of the tile once (WENO-5,
+//      Eqs. weno5_*), then per node the flux differences, the momentum
+//      derivative (Eq. derf), BGK with f^eq (Eqs. feq, g_alpha) and the RK-3
+//      combination of Eq. rk3, written to the output buffer.
+#pragma once
+
+#include "olb_kernels.cuh"
+
+namespace olb {
+
+template <typename real, int TX, int TY>
+struct FusedSmem {
+    static constexpr int HX = TX + 8, HY = TY + 6, NT = TX * TY;
+    real pop[NK][HY][HX];
+    real n[HY][HX];
+    real dp[HY][HX];
+    real ux[TY][TX];
+    real uy[TY][TX];
+    real T[TY][TX];
+    real fx[TY][TX + 1];
+    real fy[TY + 1][TX];
+    real nw[2][TY];
+};
+
+template <typename real>
+__device__ __forceinline__ real sel5(const real v[NQ], int k)
+{
+    real r = v[0];
+    r = (k == 1) ? v[1] : r;
+    r = (k == 2) ? v[2] : r;
+    r = (k == 3) ? v[3] : r;
+    r = (k == 4) ? v[4] : r;
+    return r;
+}
+
+template <typename real, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY)
+k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status, Geo g, Tab<real> t,
+        real ca, real cb, real cc)
+{
+    using S = FusedSmem<real, TX, TY>;
+    constexpr int NT = S::NT, HX = S::HX, HY = S::HY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S &sm = *reinterpret_cast<S *>(smem_raw);
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int i = x0 + tx, j = y0 + ty;
+    const bool active = (i < g.nx) && (j < g.ny);
+
+    // ---- 1. populations of the region (c <-> x = x0 - 4 + c, r <-> y = y0 - 3 + r)
+    for (int e = tid; e < HY * HX; e += NT) {
+        const int r = e / HX, c = e - r * HX;
+        const int gy = wrap(y0 - 3 + r, g.ny);
+        int gx = x0 - 4 + c;
+        const bool inside = gx >= 0 && gx < g.nx;
+        if (!g.walls) gx = wrap(gx, g.nx);
+        if (inside || !g.walls) {
+            const real *src = fs + (long long)gy * g.pitch + gx;
+#pragma unroll 5
+            for (int k = 0; k < NK; ++k) sm.pop[k][r][c] = __ldg(src + k * g.plane);
+        } else {
+#pragma unroll 5
+            for (int k = 0; k < NK; ++k) sm.pop[k][r][c] = real(0);
+        }
+    }
+    __syncthreads();
+
+    // ---- 2. moments at every fluid position of the region
+    for (int e = tid; e < HY * HX; e += NT) {
+        const int r = e / HX, c = e - r * HX;
+        const int gx = x0 - 4 + c;
+        if (g.walls && (gx < 0 || gx >= g.nx)) continue;
+        double n, jx, jy, en;
+        if constexpr (sizeof(real) == 8) {
+            double sx[NQ], sy[NQ];
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) sy[k] = 0.0;
+#pragma unroll
+            for (int k1 = 0; k1 < NQ; ++k1) {
+                double s = 0.0;
+#pragma unroll
+                for (int k2 = 0; k2 < NQ; ++k2) {
+                    const double v = (double)sm.pop[NQ * k1 + k2][r][c];
+                    s += v;
+                    sy[k2] += v;
+                }
+                sx[k1] = s;
+            }
+            n = jx = jy = en = 0.0;
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) {
+                n += sx[k];
+                jx += (double)t.R[k] * sx[k];
+                jy += (double)t.R[k] * sy[k];
+                en += (double)t.R2[k] * (sx[k] + sy[k]);
+            }
+        } else {
+            Kahan kn{0.f, 0.f}, kx{0.f, 0.f}, ky{0.f, 0.f}, ke{0.f, 0.f};
+#pragma unroll
+            for (int k1 = 0; k1 < NQ; ++k1)
+#pragma unroll
+                for (int k2 = 0; k2 < NQ; ++k2) {
+                    const float v = (float)sm.pop[NQ * k1 + k2][r][c];
+                    kn.add(v);
+                    kx.add((float)t.R[k1] * v);
+                    ky.add((float)t.R[k2] * v);
+                    ke.add(((float)t.R2[k1] + (float)t.R2[k2]) * v);
+                }
+            n = kn.value();
+            jx = kx.value();
+            jy = ky.value();
+            en = ke.value();
+        }
+        const double ux = jx / n, uy = jy / n;
+        const double T = 0.5 * (en / n - ux * ux - uy * uy);
+        // Delta p = n T - p^w, p^w = n T / (1 - b n) - a n^2 (Eq. vdw)
+        sm.n[r][c] = (real)n;
+        sm.dp[r][c] = (real)(n * T - (n * T / (1.0 - g.b * n) - g.a * n * n));
+        const int tr = r - 3, tc = c - 4;
+        if (tr >= 0 && tr < TY && tc >= 0 && tc < TX) {
+            sm.ux[tr][tc] = (real)ux;
+            sm.uy[tr][tc] = (real)uy;
+            sm.T[tr][tc] = (real)T;
+            if (x0 + tc < g.nx && y0 + tr < g.ny) {
+                const bool ok = (n > 0.0) && (T > 0.0) && (g.b * n < 1.0) && isfinite(n) && isfinite(T) &&
+                                isfinite(ux) && isfinite(uy);
+                if (!ok) atomicOr(status, 1);
+            }
+        }
+    }
+
+    // ---- 3. diffuse walls
+    const bool left_wall = g.walls && x0 == 0;
+    const bool right_wall = g.walls && (x0 + TX + 3 >= g.nx);
+    if (left_wall || right_wall) {
+        __syncthreads();
+        // mirror the fields, extrapolate the outgoing populations
+        for (int e = tid; e < HY * HX; e += NT) {
+            const int r = e / HX, c = e - r * HX;
+            const int gx = x0 - 4 + c;
+            if (gx >= 0 && gx < g.nx) continue;
+            const bool right = gx >= g.nx;
+            const int m = right ? gx - g.nx : -1 - gx;  // ghost layer 0, 1, 2
+            if (m > 2) continue;
+            const int mirror = right ? 2 * g.nx - 1 - gx : -1 - gx;
+            const int cm = mirror - (x0 - 4);
+            sm.n[r][c] = sm.n[r][cm];
+            sm.dp[r][c] = sm.dp[r][cm];
+            if (m > 1) continue;
+            // nearest three fluid nodes, nearest first
+            const int c0 = right ? g.nx - 1 - (x0 - 4) : 0 - (x0 - 4);
+            const int dc = right ? -1 : 1;
+#pragma unroll
+            for (int k1 = 0; k1 < NQ; ++k1) {
+                const bool out_going = right ? (k1 > 2) : (k1 < 2);
+                if (!out_going) continue;
+#pragma unroll
+                for (int k2 = 0; k2 < NQ; ++k2) {
+                    const int k = NQ * k1 + k2;
+                    const real a0 = sm.pop[k][r][c0], a1 = sm.pop[k][r][c0 + dc], a2 = sm.pop[k][r][c0 + 2 * dc];
+                    sm.pop[k][r][c] = m == 0 ? real(3) * a0 - real(3) * a1 + a2
+                                             : real(6) * a0 - real(8) * a1 + real(3) * a2;
+                }
+            }
+        }
+        // wall densities of the tile rows: one warp per (wall, row), lanes
+        // 0..9 take the outgoing velocities, the wall-face flux with inline
+        // extrapolated ghosts, reduced by shuffles
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int w = warp; w < 2 * TY; w += NT / 32) {
+            const int side = w / TY, tr = w - side * TY;
+            if ((side == 0 && !left_wall) || (side == 1 && !right_wall)) continue;
+            real flux = real(0);
+            if (lane < 10) {
+                const int k1 = side ? 3 + lane / 5 : lane / 5;
+                const int k = NQ * k1 + lane % 5;
+                const int c0 = side ? g.nx - 1 - (x0 - 4) : 0 - (x0 - 4);
+                const int dc = side ? -1 : 1;
+                const real a0 = sm.pop[k][tr + 3][c0], a1 = sm.pop[k][tr + 3][c0 + dc];
+                const real a2 = sm.pop[k][tr + 3][c0 + 2 * dc];
+                const real g0 = real(3) * a0 - real(3) * a1 + a2;
+                const real g1 = real(6) * a0 - real(8) * a1 + real(3) * a2;
+                flux = t.R[k1] * weno5(a2, a1, a0, g0, g1);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) flux += __shfl_xor_sync(0xffffffffu, flux, off);
+            if (lane == 0) sm.nw[side][tr] = -flux * t.inv_den[side];
+        }
+        __syncthreads();
+        // incoming ghosts (3 layers) in the tile rows: f^eq_w = n_w g g
+        for (int e = tid; e < TY * HX; e += NT) {
+            const int tr = e / HX, c = e - tr * HX;
+            const int gx = x0 - 4 + c;
+            if (gx >= 0 && gx < g.nx) continue;
+            const bool right = gx >= g.nx;
+            const int m = right ? gx - g.nx : -1 - gx;
+            if (m > 2) continue;
+            const real nwv = sm.nw[right ? 1 : 0][tr];
+#pragma unroll
+            for (int k1 = 0; k1 < NQ; ++k1) {
+                const bool in_coming = right ? (k1 < 2) : (k1 > 2);
+                if (!in_coming) continue;
+#pragma unroll
+                for (int k2 = 0; k2 < NQ; ++k2) {
+                    const int k = NQ * k1 + k2;
+                    sm.pop[k][tr + 3][c] = nwv * t.geqw[right ? 1 : 0][k];
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- 4. force and equilibrium factors at the tile node
+    real Fx = 0, Fy = 0, nn = 1, gx[NQ], gy[NQ];
+    if (active) {
+        real ddx = 0, ddy = 0, ldx = 0, ldy = 0;
+        constexpr int cy = 3, cx = 4;
+#pragma unroll
+        for (int l = 1; l <= 3; ++l)
+#pragma unroll
+            for (int m = -3; m <= 3; ++m) {
+                const int am = m < 0 ? -m : m;
+                if (grad_w(l, am) != 0.0) {
+                    const real w = real(l * grad_w(l, am));
+                    ddx += w * (sm.dp[ty + cy + m][tx + cx + l] - sm.dp[ty + cy + m][tx + cx - l]);
+                    ddy += w * (sm.dp[ty + cy + l][tx + cx + m] - sm.dp[ty + cy - l][tx + cx + m]);
+                }
+                if (glap_c(am, l) != 0.0) {
+                    const real w = real(glap_c(am, l));
+                    ldx += w * (sm.n[ty + cy + m][tx + cx + l] - sm.n[ty + cy + m][tx + cx - l]);
+                    ldy += w * (sm.n[ty + cy + l][tx + cx + m] - sm.n[ty + cy - l][tx + cx + m]);
+                }
+            }
+        nn = sm.n[ty + cy][tx + cx];
+        Fx = ddx * real(g.inv_ds) / nn + real(g.sigma) * ldx * real(g.inv_ds3);
+        Fy = ddy * real(g.inv_ds) / nn + real(g.sigma) * ldy * real(g.inv_ds3);
+        eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], gx);
+        eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gy);
+    }
+
+    // ---- 5. advection, collision and RK combination, one velocity at a time
+    const int nfx = (TX + 1) * TY, nfy = TX * (TY + 1);
+    const long long o = (long long)j * g.pitch + i;
+    const real itau = real(g.inv_tau);
+    const real cadv = cc * real(g.inv_ds);
+    for (int k = 0; k < NK; ++k) {
+        const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
+        const int nx_faces = (k1 == 2) ? 0 : nfx;
+        const int ny_faces = (k2 == 2) ? 0 : nfy;
+        if (k > 0) __syncthreads();  // the previous velocity's faces are consumed
+        for (int e = tid; e < nx_faces + ny_faces; e += NT) {
+            if (e < nx_faces) {
+                const int r = e / (TX + 1), c = e - r * (TX + 1);
+                if (y0 + r < g.ny && x0 + c <= g.nx) {
+                    // face at x = x0 + c: nodes x0+c-3 .. x0+c+2 are columns c+1 .. c+6
+                    const real *row = &sm.pop[k][3 + r][0];
+                    sm.fx[r][c] = (k1 > 2) ? weno5(row[c + 1], row[c + 2], row[c + 3], row[c + 4], row[c + 5])
+                                           : weno5(row[c + 6], row[c + 5], row[c + 4], row[c + 3], row[c + 2]);
+                }
+            } else {
+                const int e2 = e - nx_faces;
+                const int r = e2 / TX, c = e2 - r * TX;
+                if (x0 + c < g.nx && y0 + r <= g.ny) {
+                    // face at y = y0 + r: rows y0+r-3 .. y0+r+2 are rows r .. r+5
+                    const int cc4 = 4 + c;
+                    const real(*P)[HX] = sm.pop[k];
+                    sm.fy[r][c] = (k2 > 2) ? weno5(P[r][cc4], P[r + 1][cc4], P[r + 2][cc4], P[r + 3][cc4], P[r + 4][cc4])
+                                           : weno5(P[r + 5][cc4], P[r + 4][cc4], P[r + 3][cc4], P[r + 2][cc4],
+                                                   P[r + 1][cc4]);
+                }
+            }
+        }
+        __syncthreads();
+        if (active) {
+            const int r = ty + 3, c = tx + 4;
+            real dx = 0, dy = 0;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                dx += t.D[k1][q] * sm.pop[NQ * q + k2][r][c];
+                dy += t.D[k2][q] * sm.pop[NQ * k1 + q][r][c];
+            }
+            const real f = sm.pop[k][r][c];
+            const real feq = nn * sel5(gx, k1) * sel5(gy, k2);
+            real adv = 0;
+            if (k1 != 2) adv += t.R[k1] * (sm.fx[ty][tx + 1] - sm.fx[ty][tx]);
+            if (k2 != 2) adv += t.R[k2] * (sm.fy[ty + 1][tx] - sm.fy[ty][tx]);
+            const real Lloc = -(Fx * dx + Fy * dy) - (f - feq) * itau;
+            real v = cb * f + cc * Lloc - cadv * adv;
+            if (ca != real(0)) v += ca * fn[k * g.plane + o];
+            out[k * g.plane + o] = v;
+        }
+    }
+}
+
+// Tile shapes compiled for each precision; the context picks one per grid.
+template <typename real, int TX, int TY>
+cudaError_t fused_prepare_one()
+{
+    return cudaFuncSetAttribute(k_fused<real, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(FusedSmem<real, TX, TY>));
+}
+
+template <typename real, int TX, int TY>
+cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *status, const Geo &g,
+                             const Tab<real> &t, StageCoef c, cudaStream_t s)
+{
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
+    k_fused<real, TX, TY><<<grid, TX * TY, sizeof(FusedSmem<real, TX, TY>), s>>>(
+        fs, fn, out, status, g, t, (real)c.ca, (real)c.cb, (real)c.cc);
+    return cudaGetLastError();
+}
+
+// Tile shapes compiled for each precision (TX x TY nodes per CTA); the
+// context picks one per grid (olb_set_tile overrides).
+#define OLB_FUSED_SHAPE_CASES(real, DO) DO(real, 8, 8) DO(real, 16, 8) DO(real, 32, 8) DO(real, 32, 16)
+#define OLB_FUSED_PREP_CASE(real, A, B) \
+    if (tx == A && ty == B) return fused_prepare_one<real, A, B>();
+#define OLB_FUSED_LAUNCH_CASE(real, A, B) \
+    if (tx == A && ty == B) return fused_launch_one<real, A, B>(fs, fn, out, status, g, t, c, s);
+#define OLB_DEFINE_FUSED(real)                                                                                \
+    cudaError_t prepare_fused(real *, int tx, int ty)                                                         \
+    {                                                                                                         \
+        OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_PREP_CASE)                                                      \
+        return cudaErrorInvalidValue;                                                                         \
+    }                                                                                                         \
+    cudaError_t launch_fused(const real *fs, const real *fn, real *out, int *status, const Geo &g,            \
+                             const Tab<real> &t, StageCoef c, int tx, int ty, cudaStream_t s)                 \
+    {                                                                                                         \
+        OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_LAUNCH_CASE)                                                    \
+        return cudaErrorInvalidValue;                                                                         \
+    }
+
+}  // namespace olb

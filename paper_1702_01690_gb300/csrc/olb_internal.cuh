@@ -4,11 +4,9 @@
 //   populations  real f[25][ny][pitch]   kappa = 5*k1 + k2 (x-major velocity
 //                index), pitch = nx rounded up to 32 elements so every row
 //                starts on a 128/256-byte boundary
-//   stage fields real fld[5][ny][pitch]  n, u_x, u_y, T, Delta p of the stage
-//                input (written by the moments kernel, read by the stage
-//                kernel with a 3-node halo)
-//   wall density real nw[2][ny]          n_w of Eq. nw per wall and row
 //   status       int                     bit 0: invalid moment seen
+// The stage kernel keeps moments, force and wall densities of its tile in
+// shared memory; no other global scratch is needed.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -54,14 +52,11 @@ struct StageCoef {
 };
 
 // Launchers, one set per precision (olb_fp64.cu, olb_fp32.cu).  Output
-// pointers of moments_out may be NULL to skip a field.
+// pointers of launch_moments_out may be NULL to skip a field.
 #define OLB_DECLARE_LAUNCHERS(real)                                                                    \
-    cudaError_t prepare(real *);                                                                       \
-    cudaError_t launch_moments(const real *f, real *fld, real *nw, int *status, const Geo &g,          \
-                               const Tab<real> &t, cudaStream_t s);                                     \
-    cudaError_t launch_stage(const real *fs, const real *fn, real *out, const real *fld,                \
-                             const real *nw, const Geo &g, const Tab<real> &t, StageCoef c,             \
-                             cudaStream_t s);                                                           \
+    cudaError_t prepare_fused(real *, int tx, int ty);                                                 \
+    cudaError_t launch_fused(const real *fs, const real *fn, real *out, int *status, const Geo &g,     \
+                             const Tab<real> &t, StageCoef c, int tx, int ty, cudaStream_t s);         \
     cudaError_t launch_init(real *f, const double *n, const double *ux, const double *uy,              \
                             const double *T, const Geo &g, const Tab<real> &t, cudaStream_t s);         \
     cudaError_t launch_moments_out(const real *f, double *n, double *ux, double *uy, double *T,        \
@@ -71,5 +66,10 @@ struct StageCoef {
 
 OLB_DECLARE_LAUNCHERS(double)
 OLB_DECLARE_LAUNCHERS(float)
+
+// Stage-kernel tile shapes compiled for both precisions.
+constexpr int NUM_TILES = 4;
+constexpr int TILE_X[NUM_TILES] = {8, 16, 32, 32};
+constexpr int TILE_Y[NUM_TILES] = {8, 8, 8, 16};
 
 }  // namespace olb

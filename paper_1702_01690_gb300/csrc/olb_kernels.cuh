@@ -1,18 +1,8 @@
-// olb_kernels.cuh -- device code of one RK-3 stage, templated on the
-// population precision (double, or float with Kahan-compensated moments).
-//
-// Per stage two kernels run:
-//   k_moments  one thread per node: n, u, T, Delta p from the 25 populations
-//              (Sec. 2.2, Eq. vdw); extra warps, one per (wall, row), form the
-//              WENO flux of the 10 outgoing velocities at the wall face and
-//              reduce it with warp shuffles into n_w (Eq. nw).
-//   k_stage    one CTA per TX x TY tile, one thread per node: force from the
-//              49-point stencils on a shared-memory tile of Delta p and n with a
-//              3-node halo (Eqs. F_def, stencil_grad, stencil_glap), the local
-//              part of L (momentum derivative Eq. derf, BGK with Eq. feq),
-//              then for each velocity the WENO-5 face fluxes of a shared-memory
-//              population tile (Eqs. weno5_*), each face computed once, and
-//              the RK-3 combination of Eq. rk3.
+// olb_kernels.cuh -- device building blocks shared by the stage kernel
+// (olb_fused.cuh): stencil coefficients, WENO-5, equilibrium factors, Kahan
+// sums, and the initialisation / moment-output / conversion kernels,
+// templated on the population precision (double, or float with
+// Kahan-compensated moments).
 #pragma once
 
 #include "olb_internal.cuh"
@@ -218,234 +208,6 @@ __device__ __forceinline__ void node_sums<float>(const float *__restrict__ f, lo
     e = ke.value();
 }
 
-// ---------------------------------------------------------------- K1
-constexpr int MOM_THREADS = 256;
-
-template <typename real>
-__global__ void __launch_bounds__(MOM_THREADS)
-k_moments(const real *__restrict__ f, real *__restrict__ fld, real *__restrict__ nw,
-          int *__restrict__ status, Geo g, Tab<real> t, int node_blocks)
-{
-    if ((int)blockIdx.x < node_blocks) {
-        const long long idx = (long long)blockIdx.x * MOM_THREADS + threadIdx.x;
-        if (idx >= (long long)g.nx * g.ny) return;
-        const int j = (int)(idx / g.nx), i = (int)(idx - (long long)j * g.nx);
-        const long long o = (long long)j * g.pitch + i;
-        double n, jx, jy, e;
-        node_sums<real>(f, g.plane, o, t, n, jx, jy, e);
-        const double ux = jx / n, uy = jy / n;
-        const double T = 0.5 * (e / n - ux * ux - uy * uy);
-        // Delta p = n T - p^w, p^w = n T / (1 - b n) - a n^2 (Eq. vdw)
-        const double dp = n * T - (n * T / (1.0 - g.b * n) - g.a * n * n);
-        fld[0 * g.plane + o] = (real)n;
-        fld[1 * g.plane + o] = (real)ux;
-        fld[2 * g.plane + o] = (real)uy;
-        fld[3 * g.plane + o] = (real)T;
-        fld[4 * g.plane + o] = (real)dp;
-        const bool ok = (n > 0.0) && (T > 0.0) && (g.b * n < 1.0) && isfinite(n) && isfinite(T) &&
-                        isfinite(ux) && isfinite(uy);
-        if (!ok) atomicOr(status, 1);
-        return;
-    }
-    // Wall densities: one warp per (wall, row); lanes 0..9 take the outgoing
-    // velocities (p_x < 0 at the left wall, p_x > 0 at the right wall).
-    const int warp = ((int)blockIdx.x - node_blocks) * (MOM_THREADS / 32) + (int)(threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (warp >= 2 * g.ny) return;
-    const int side = warp / g.ny, j = warp - side * g.ny;
-    real flux = real(0);
-    if (lane < 10) {
-        const int k1 = side ? 3 + lane / 5 : lane / 5;
-        const int k2 = lane % 5;
-        const real *fp = f + (NQ * k1 + k2) * g.plane + (long long)j * g.pitch;
-        // nearest three fluid nodes, nearest first
-        const real a0 = side ? fp[g.nx - 1] : fp[0];
-        const real a1 = side ? fp[g.nx - 2] : fp[1];
-        const real a2 = side ? fp[g.nx - 3] : fp[2];
-        // quadratic extrapolation into the first two ghost layers (Sec. 3.4.2)
-        const real g0 = real(3) * a0 - real(3) * a1 + a2;
-        const real g1 = real(6) * a0 - real(8) * a1 + real(3) * a2;
-        // upwind-ordered stencil of the wall face, mirrored for the left wall
-        flux = t.R[k1] * weno5(a2, a1, a0, g0, g1);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) flux += __shfl_xor_sync(0xffffffffu, flux, off);
-    if (lane == 0) nw[side * g.ny + j] = -flux * t.inv_den[side];
-}
-
-// ---------------------------------------------------------------- K2
-template <typename real, int TX, int TY>
-struct StageSmem {
-    static constexpr int NT = TX * TY, HX = TX + 6, HY = TY + 6;
-    real dp[HY][HX];
-    real n[HY][HX];
-    real f[HY][HX];
-    real fx[TY][TX + 1];
-    real fy[TY + 1][TX];
-    real part[NK][NT];
-};
-
-template <typename real, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY)
-k_stage(const real *__restrict__ fs, const real *fn, real *out, const real *__restrict__ fld,
-        const real *__restrict__ nw, Geo g, Tab<real> t, real ca, real cb, real cc)
-{
-    using S = StageSmem<real, TX, TY>;
-    constexpr int NT = S::NT, HX = S::HX, HY = S::HY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    S &sm = *reinterpret_cast<S *>(smem_raw);
-
-    const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int i = x0 + tx, j = y0 + ty;
-    const bool active = (i < g.nx) && (j < g.ny);
-    const long long o = (long long)j * g.pitch + i;
-
-    // ---- Delta p and n tile with a 3-node halo (field rule of Sec. 3.4.3)
-    for (int e = tid; e < HX * HY; e += NT) {
-        const int r = e / HX, c = e - r * HX;
-        const int gx = g.walls ? reflect(x0 - 3 + c, g.nx) : wrap(x0 - 3 + c, g.nx);
-        const int gy = wrap(y0 - 3 + r, g.ny);
-        const long long go = (long long)gy * g.pitch + gx;
-        sm.n[r][c] = __ldg(fld + 0 * g.plane + go);
-        sm.dp[r][c] = __ldg(fld + 4 * g.plane + go);
-    }
-    __syncthreads();
-
-    // ---- local part of L and the non-advective part of the RK combination
-    if (active) {
-        real ddx = 0, ddy = 0, ldx = 0, ldy = 0;
-#pragma unroll
-        for (int l = 1; l <= 3; ++l)
-#pragma unroll
-            for (int m = -3; m <= 3; ++m) {
-                const int am = m < 0 ? -m : m;
-                constexpr int cy = 3, cx = 3;
-                if (grad_w(l, am) != 0.0) {
-                    const real w = real(l * grad_w(l, am));
-                    ddx += w * (sm.dp[ty + cy + m][tx + cx + l] - sm.dp[ty + cy + m][tx + cx - l]);
-                    ddy += w * (sm.dp[ty + cy + l][tx + cx + m] - sm.dp[ty + cy - l][tx + cx + m]);
-                }
-                if (glap_c(am, l) != 0.0) {
-                    const real w = real(glap_c(am, l));
-                    ldx += w * (sm.n[ty + cy + m][tx + cx + l] - sm.n[ty + cy + m][tx + cx - l]);
-                    ldy += w * (sm.n[ty + cy + l][tx + cx + m] - sm.n[ty + cy - l][tx + cx + m]);
-                }
-            }
-        const real nn = sm.n[ty + 3][tx + 3];
-        const real ux = __ldg(fld + 1 * g.plane + o);
-        const real uy = __ldg(fld + 2 * g.plane + o);
-        const real T = __ldg(fld + 3 * g.plane + o);
-        // force (Eq. F_def): F = grad(Delta p)/n + sigma grad(Laplacian n)
-        const real Fx = ddx * real(g.inv_ds) / nn + real(g.sigma) * ldx * real(g.inv_ds3);
-        const real Fy = ddy * real(g.inv_ds) / nn + real(g.sigma) * ldy * real(g.inv_ds3);
-        real gx[NQ], gy[NQ];
-        eq_factors<real>(t, ux, T, gx);
-        eq_factors<real>(t, uy, T, gy);
-        real fv[NK];
-#pragma unroll
-        for (int k = 0; k < NK; ++k) fv[k] = __ldg(fs + k * g.plane + o);
-        const real itau = real(g.inv_tau);
-#pragma unroll
-        for (int k1 = 0; k1 < NQ; ++k1)
-#pragma unroll
-            for (int k2 = 0; k2 < NQ; ++k2) {
-                real dx = 0, dy = 0;
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    dx += t.D[k1][q] * fv[NQ * q + k2];
-                    dy += t.D[k2][q] * fv[NQ * k1 + q];
-                }
-                const int k = NQ * k1 + k2;
-                const real feq = nn * gx[k1] * gy[k2];
-                const real Lloc = -(Fx * dx + Fy * dy) - (fv[k] - feq) * itau;
-                real p = cb * fv[k] + cc * Lloc;
-                if (ca != real(0)) p += ca * fn[k * g.plane + o];
-                sm.part[k][tid] = p;
-            }
-    }
-
-    // ---- advection, one velocity at a time
-    const int nfx = (TX + 1) * TY, nfy = TX * (TY + 1);
-    for (int k = 0; k < NK; ++k) {
-        const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
-        const real px = t.R[k1], py = t.R[k2];
-        const real *fk = fs + k * g.plane;
-        __syncthreads();  // previous velocity's faces are consumed
-        // population tile: rows of the tile with the x halo, columns of the
-        // tile with the y halo (corners are never read)
-        for (int e = tid; e < TY * HX + 6 * TX; e += NT) {
-            int r, c;
-            if (e < TY * HX) {
-                r = 3 + e / HX;
-                c = e - (r - 3) * HX;
-            } else {
-                const int e2 = e - TY * HX;
-                const int rr = e2 / TX;
-                r = rr < 3 ? rr : TY + rr;
-                c = 3 + (e2 - rr * TX);
-            }
-            const int gy = wrap(y0 - 3 + r, g.ny);
-            int gx = x0 - 3 + c;
-            real v;
-            if (gx >= 0 && gx < g.nx) {
-                v = __ldg(fk + (long long)gy * g.pitch + gx);
-            } else if (!g.walls) {
-                v = __ldg(fk + (long long)gy * g.pitch + wrap(gx, g.nx));
-            } else {
-                // diffuse-wall ghosts (Sec. 3.4.2)
-                const bool right = gx >= g.nx;
-                const int m = right ? gx - g.nx : -1 - gx;
-                const bool out_going = right ? (k1 > 2) : (k1 < 2);
-                const bool in_coming = right ? (k1 < 2) : (k1 > 2);
-                v = real(0);
-                if (m <= 1 && out_going) {
-                    const real *row = fk + (long long)gy * g.pitch;
-                    const real a0 = right ? __ldg(row + g.nx - 1) : __ldg(row + 0);
-                    const real a1 = right ? __ldg(row + g.nx - 2) : __ldg(row + 1);
-                    const real a2 = right ? __ldg(row + g.nx - 3) : __ldg(row + 2);
-                    v = m == 0 ? real(3) * a0 - real(3) * a1 + a2 : real(6) * a0 - real(8) * a1 + real(3) * a2;
-                } else if (m <= 2 && in_coming) {
-                    v = __ldg(nw + (right ? g.ny : 0) + gy) * t.geqw[right ? 1 : 0][k];
-                }
-            }
-            sm.f[r][c] = v;
-        }
-        __syncthreads();
-        // faces: x faces of the tile rows, then y faces of the tile columns
-        const int nx_faces = (k1 == 2) ? 0 : nfx;
-        const int ny_faces = (k2 == 2) ? 0 : nfy;
-        for (int e = tid; e < nx_faces + ny_faces; e += NT) {
-            if (e < nx_faces) {
-                const int r = e / (TX + 1), c = e - r * (TX + 1);
-                if (y0 + r < g.ny && x0 + c <= g.nx) {
-                    const real *row = &sm.f[3 + r][0];
-                    sm.fx[r][c] = (k1 > 2) ? weno5(row[c], row[c + 1], row[c + 2], row[c + 3], row[c + 4])
-                                           : weno5(row[c + 5], row[c + 4], row[c + 3], row[c + 2], row[c + 1]);
-                }
-            } else {
-                const int e2 = e - nx_faces;
-                const int r = e2 / TX, c = e2 - r * TX;
-                if (x0 + c < g.nx && y0 + r <= g.ny) {
-                    const int cc3 = 3 + c;
-                    sm.fy[r][c] = (k2 > 2) ? weno5(sm.f[r][cc3], sm.f[r + 1][cc3], sm.f[r + 2][cc3],
-                                                   sm.f[r + 3][cc3], sm.f[r + 4][cc3])
-                                           : weno5(sm.f[r + 5][cc3], sm.f[r + 4][cc3], sm.f[r + 3][cc3],
-                                                   sm.f[r + 2][cc3], sm.f[r + 1][cc3]);
-                }
-            }
-        }
-        __syncthreads();
-        if (active) {
-            real adv = 0;
-            if (k1 != 2) adv += px * (sm.fx[ty][tx + 1] - sm.fx[ty][tx]);
-            if (k2 != 2) adv += py * (sm.fy[ty + 1][tx] - sm.fy[ty][tx]);
-            out[k * g.plane + o] = sm.part[k][tid] - cc * (adv * real(g.inv_ds));
-        }
-    }
-}
-
 // ---------------------------------------------------------------- init / output
 template <typename real>
 __global__ void k_init(real *__restrict__ f, const double *__restrict__ n, const double *__restrict__ ux,
@@ -508,32 +270,9 @@ __global__ void k_from_f64(real *__restrict__ f, const double *__restrict__ src,
 }
 
 // ---------------------------------------------------------------- launchers
-// Instantiated once per precision by olb_fp64.cu / olb_fp32.cu with the
-// stage tile TX x TY chosen there.
-#define OLB_DEFINE_LAUNCHERS(real, TX, TY)                                                                   \
-    cudaError_t prepare(real *)                                                                              \
-    {                                                                                                        \
-        return cudaFuncSetAttribute(k_stage<real, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                                    (int)sizeof(StageSmem<real, TX, TY>));                                   \
-    }                                                                                                        \
-    cudaError_t launch_moments(const real *f, real *fld, real *nw, int *status, const Geo &g,                \
-                               const Tab<real> &t, cudaStream_t s)                                           \
-    {                                                                                                        \
-        const long long N = (long long)g.nx * g.ny;                                                          \
-        const int node_blocks = (int)((N + MOM_THREADS - 1) / MOM_THREADS);                                  \
-        const int wall_blocks = g.walls ? (2 * g.ny + MOM_THREADS / 32 - 1) / (MOM_THREADS / 32) : 0;        \
-        k_moments<real><<<node_blocks + wall_blocks, MOM_THREADS, 0, s>>>(f, fld, nw, status, g, t,          \
-                                                                          node_blocks);                      \
-        return cudaGetLastError();                                                                           \
-    }                                                                                                        \
-    cudaError_t launch_stage(const real *fs, const real *fn, real *out, const real *fld, const real *nw,     \
-                             const Geo &g, const Tab<real> &t, StageCoef c, cudaStream_t s)                  \
-    {                                                                                                        \
-        dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);                                               \
-        k_stage<real, TX, TY><<<grid, TX * TY, sizeof(StageSmem<real, TX, TY>), s>>>(                        \
-            fs, fn, out, fld, nw, g, t, (real)c.ca, (real)c.cb, (real)c.cc);                                 \
-        return cudaGetLastError();                                                                           \
-    }                                                                                                        \
+// Initialisation, moment output and FP64 conversion kernels (one instance
+// per precision, defined in olb_fp64.cu / olb_fp32.cu).
+#define OLB_DEFINE_AUX_LAUNCHERS(real)                                                                       \
     cudaError_t launch_init(real *f, const double *n, const double *ux, const double *uy, const double *T,   \
                             const Geo &g, const Tab<real> &t, cudaStream_t s)                                \
     {                                                                                                        \

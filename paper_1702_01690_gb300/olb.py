@@ -29,7 +29,7 @@ WENO_JS = 0
 SYMBOLS = ("olb_set_allocator", "olb_create", "olb_destroy", "olb_init_fields",
            "olb_init_fields_device", "olb_step", "olb_step_async", "olb_get_status",
            "olb_moments", "olb_moments_device", "olb_get_populations",
-           "olb_set_populations", "olb_status_string", "olb_profile")
+           "olb_set_populations", "olb_status_string", "olb_profile", "olb_set_tile", "olb_get_tile")
 
 
 class Params(ctypes.Structure):
@@ -65,6 +65,10 @@ for _n in ("olb_get_populations", "olb_set_populations"):
     getattr(_lib, _n).argtypes = [_VP, _VP]
     getattr(_lib, _n).restype = ctypes.c_int
 _lib.olb_profile.argtypes = [_VP, ctypes.c_int, _VP, _VP]
+_lib.olb_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+_lib.olb_set_tile.restype = ctypes.c_int
+_lib.olb_get_tile.argtypes = [_VP, _VP, _VP]
+_lib.olb_get_tile.restype = ctypes.c_int
 _lib.olb_profile.restype = ctypes.c_int
 _lib.olb_status_string.argtypes = [ctypes.c_int]
 _lib.olb_status_string.restype = ctypes.c_char_p
@@ -213,13 +217,21 @@ class Context:
         return tuple(out)
 
     def profile(self, nsteps: int):
-        """Mean device ms per launch of (moments, stage) and launch counts."""
-        ms = np.zeros(2)
-        cnt = np.zeros(2, dtype=np.int32)
+        """Mean device ms per launch of the stage kernel and the launch count."""
+        ms = np.zeros(1)
+        cnt = np.zeros(1, dtype=np.int32)
         _check(_lib.olb_profile(self._h, int(nsteps), ms.ctypes.data_as(_VP), cnt.ctypes.data_as(_VP)),
                "olb_profile")
-        return {"moments_ms": float(ms[0]), "stage_ms": float(ms[1]),
-                "moments_launches": int(cnt[0]), "stage_launches": int(cnt[1])}
+        return {"stage_ms": float(ms[0]), "stage_launches": int(cnt[0])}
+
+    def set_tile(self, tx: int, ty: int) -> None:
+        _check(_lib.olb_set_tile(self._h, int(tx), int(ty)), "olb_set_tile")
+
+    def get_tile(self):
+        a = ctypes.c_int()
+        b = ctypes.c_int()
+        _check(_lib.olb_get_tile(self._h, ctypes.byref(a), ctypes.byref(b)), "olb_get_tile")
+        return a.value, b.value
 
     def get_populations(self) -> np.ndarray:
         out = np.zeros((25, self.ny, self.nx))
