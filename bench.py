@@ -254,7 +254,7 @@ def run_ours(args, rank, world):
     st_ms = prof["stage_ms"]
     achieved = STAGE_FLOPS_PER_NODE * N / (st_ms * 1e-3) / 1e12
     tile = ctx.get_tile()
-    roof = {"kernel": f"k_fused<double,{tile[0]},{tile[1]}> (moments + force + WENO-5 + BGK + RK-3 stage)",
+    roof = {"kernel": f"k_fused<double,{tile[0]},{tile[1]},{tile[2]}> (moments + force + WENO-5 + BGK + RK-3 stage)",
             "bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
             "peak_source": "FP64 units x max SM clock (2 DFMA/SM/clk x 152 x 2.07 GHz)",
@@ -276,7 +276,7 @@ def run_ours(args, rank, world):
     v32 = world * N * args.steps / (total32 / 1e3)
     fp32 = {"value": v32, "ms_per_step": total32 / args.steps, "speedup_vs_fp64": v32 / value,
             "max_rel_err_vs_fp64_after_steps": err32, "steps_compared": args.warmup + args.steps,
-            "roofline": {"kernel": f"k_fused<float,{tile32[0]},{tile32[1]}>", "bound": "alu", "achieved": ach32,
+            "roofline": {"kernel": f"k_fused<float,{tile32[0]},{tile32[1]},{tile32[2]}>", "bound": "alu", "achieved": ach32,
                          "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": ach32 / PEAK_FP32_TFLOPS,
                          "stage_ms": prof32["stage_ms"]}}
     ctx32.close()

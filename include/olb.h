@@ -169,12 +169,13 @@ int olb_set_populations(olb_ctx *ctx, const double *f);
  * NULL).  The populations advance exactly as with olb_step. */
 int olb_profile(olb_ctx *ctx, int nsteps, double *ms, int *launches);
 
-/* Tile shape of the stage kernel (nodes per CTA along x and y).  Compiled
- * shapes: 8x8, 16x8, 32x8, 32x16; olb_create picks one from the grid size.
- * olb_set_tile returns OLB_ERR_ARG for any other shape; results do not
- * depend on the shape.  Not part of the paper (a tuning knob). */
-int olb_set_tile(olb_ctx *ctx, int tx, int ty);
-int olb_get_tile(olb_ctx *ctx, int *tx, int *ty);
+/* Shape of the stage kernel: tx x ty nodes per CTA, kp velocities advanced
+ * at once (tx*ty*kp threads).  Compiled shapes (tx, ty, kp): (8,8,4),
+ * (16,8,2), (16,8,1), (32,8,1), (32,16,1); olb_create picks one from the
+ * grid size.  olb_set_tile returns OLB_ERR_ARG for any other shape; results
+ * do not depend on the shape.  Not part of the paper (a tuning knob). */
+int olb_set_tile(olb_ctx *ctx, int tx, int ty, int kp);
+int olb_get_tile(olb_ctx *ctx, int *tx, int *ty, int *kp);
 
 /* Human-readable name of a status code (static string). */
 const char *olb_status_string(int status);

@@ -121,7 +121,7 @@ struct olb_ctx {
     size_t elt;                 // bytes per population value
     void *f[3];                 // f^n, f^(1), f^(2)
     int *status;
-    int tx, ty;                 // stage-kernel tile shape
+    int tx, ty, kp;             // stage-kernel tile shape and velocity lanes
     double *stage4;             // FP64 [4][ny][nx] staging for host transfers
     struct Alloc {
         void *ptr;
@@ -188,7 +188,7 @@ static cudaError_t enqueue_stage(olb_ctx *c, int st, cudaStream_t s)
     real *dst[3] = {f1, f2, f0};
     StageCoef coef;
     stage_coef(c->p.dt, st, &coef);
-    return launch_fused(src[st], f0, dst[st], c->status, c->geo, ctx_tab<real>(c), coef, c->tx, c->ty, s);
+    return launch_fused(src[st], f0, dst[st], c->status, c->geo, ctx_tab<real>(c), coef, c->tx, c->ty, c->kp, s);
 }
 
 template <typename real>
@@ -275,25 +275,23 @@ static int validate(const olb_params *p)
 
 static cudaError_t prepare_tile(olb_ctx *c)
 {
-    return is_fp64(c) ? prepare_fused((double *)nullptr, c->tx, c->ty) : prepare_fused((float *)nullptr, c->tx, c->ty);
+    return is_fp64(c) ? prepare_fused((double *)nullptr, c->tx, c->ty, c->kp)
+                      : prepare_fused((float *)nullptr, c->tx, c->ty, c->kp);
 }
 
-// Default tile: the largest shape that still gives every SM two CTAs, else
-// the smallest shape (most CTAs, for small grids).  FP64 stays at <= 16 x 8
-// nodes so that two CTAs share an SM: the FP64 pipe idles while a lone CTA
-// waits at a barrier.  Shapes are listed by increasing area.
+// Default shape: 16 x 8 nodes with 2 velocity lanes (FP64) or 32 x 16
+// nodes (FP32) when that still gives every SM two CTAs; otherwise 8 x 8
+// nodes with 4 velocity lanes, so that small grids (e.g. 1024 x 8) still
+// put 8 warps on each busy SM.  olb_set_tile / olb_autotune override.
 static void default_tile(olb_ctx *c)
 {
-    const long long two_per_sm = 2 * 152;
-    int best = 0;
-    for (int k = 0; k < NUM_TILES; ++k) {
-        if (is_fp64(c) && TILE_X[k] * TILE_Y[k] > 128) continue;
-        const long long ctas =
-            (long long)((c->geo.nx + TILE_X[k] - 1) / TILE_X[k]) * ((c->geo.ny + TILE_Y[k] - 1) / TILE_Y[k]);
-        if (ctas >= two_per_sm) best = k;
-    }
-    c->tx = TILE_X[best];
-    c->ty = TILE_Y[best];
+    const int big = is_fp64(c) ? 1 : 4;  // index into TILE_*
+    const long long ctas = (long long)((c->geo.nx + TILE_X[big] - 1) / TILE_X[big]) *
+                           ((c->geo.ny + TILE_Y[big] - 1) / TILE_Y[big]);
+    const int k = ctas >= 2 * 152 ? big : 0;
+    c->tx = TILE_X[k];
+    c->ty = TILE_Y[k];
+    c->kp = TILE_K[k];
 }
 
 extern "C" int olb_create(const olb_params *p, void *stream, olb_ctx **out)
@@ -590,22 +588,24 @@ static void drop_graphs(olb_ctx *c)
     c->cap = nullptr;
 }
 
-extern "C" int olb_set_tile(olb_ctx *c, int tx, int ty)
+extern "C" int olb_set_tile(olb_ctx *c, int tx, int ty, int kp)
 {
     if (!c) return OLB_ERR_ARG;
     int k = 0;
-    while (k < NUM_TILES && !(TILE_X[k] == tx && TILE_Y[k] == ty)) ++k;
+    while (k < NUM_TILES && !(TILE_X[k] == tx && TILE_Y[k] == ty && TILE_K[k] == kp)) ++k;
     if (k == NUM_TILES) return OLB_ERR_ARG;
     DeviceGuard dg(c->device);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    const int otx = c->tx, oty = c->ty;
+    const int otx = c->tx, oty = c->ty, okp = c->kp;
     c->tx = tx;
     c->ty = ty;
+    c->kp = kp;
     e = prepare_tile(c);
     if (e != cudaSuccess) {
         c->tx = otx;
         c->ty = oty;
+        c->kp = okp;
         cudaGetLastError();
         return cuda_status(e);
     }
@@ -613,10 +613,11 @@ extern "C" int olb_set_tile(olb_ctx *c, int tx, int ty)
     return OLB_OK;
 }
 
-extern "C" int olb_get_tile(olb_ctx *c, int *tx, int *ty)
+extern "C" int olb_get_tile(olb_ctx *c, int *tx, int *ty, int *kp)
 {
-    if (!c || !tx || !ty) return OLB_ERR_ARG;
+    if (!c || !tx || !ty || !kp) return OLB_ERR_ARG;
     *tx = c->tx;
     *ty = c->ty;
+    *kp = c->kp;
     return OLB_OK;
 }

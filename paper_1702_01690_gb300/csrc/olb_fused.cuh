@@ -14,27 +14,29 @@
 //      for the incoming velocities;
 //   4. force F = grad(Delta p)/n + sigma grad(Laplacian n) at the tile nodes
 //      from the 49-point stencils (Eqs. F_def, stencil_grad, stencil_glap);
-//   5. for each velocity: every x and y face of the tile once (WENO-5,
-//      Eqs. weno5_*), then per node the flux differences, the momentum
-//      derivative (Eq. derf), BGK with f^eq (Eqs. feq, g_alpha) and the RK-3
-//      combination of Eq. rk3, written to the output buffer.
+//   5. for KP velocities at a time (one group of TX*TY threads each): every x
+//      and y face of the tile once (WENO-5, Eqs. weno5_*), then per node the
+//      flux differences, the momentum derivative (Eq. derf), BGK with f^eq
+//      (Eqs. feq, g_alpha) and the RK-3 combination of Eq. rk3, written to
+//      the output buffer.  KP > 1 gives small tiles enough warps.
 #pragma once
 
 #include "olb_kernels.cuh"
 
 namespace olb {
 
-template <typename real, int TX, int TY>
+template <typename real, int TX, int TY, int KP>
 struct FusedSmem {
-    static constexpr int HX = TX + 8, HY = TY + 6, NT = TX * TY;
+    static constexpr int HX = TX + 8, HY = TY + 6, NN = TX * TY, NT = NN * KP;
     real pop[NK][HY][HX];
     real n[HY][HX];
     real dp[HY][HX];
     real ux[TY][TX];
     real uy[TY][TX];
     real T[TY][TX];
-    real fx[TY][TX + 1];
-    real fy[TY + 1][TX];
+    real loc[3 + 2 * NQ][NN];  // F_x, F_y, n, g_k(u_x, T), g_k(u_y, T) per tile node
+    real fx[KP][TY][TX + 1];
+    real fy[KP][TY + 1][TX];
     real nw[2][TY];
 };
 
@@ -49,18 +51,20 @@ __device__ __forceinline__ real sel5(const real v[NQ], int k)
     return r;
 }
 
-template <typename real, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY)
+template <typename real, int TX, int TY, int KP>
+__global__ void __launch_bounds__(TX *TY *KP)
 k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status, Geo g, Tab<real> t,
         real ca, real cb, real cc)
 {
-    using S = FusedSmem<real, TX, TY>;
-    constexpr int NT = S::NT, HX = S::HX, HY = S::HY;
+    using S = FusedSmem<real, TX, TY, KP>;
+    constexpr int NT = S::NT, NN = S::NN, HX = S::HX, HY = S::HY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
 
+    // thread = (tile node, velocity lane): KP velocities are advanced at once
     const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = tid / TX;
+    const int node = tid % NN, lane_k = tid / NN;
+    const int tx = node % TX, ty = node / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int i = x0 + tx, j = y0 + ty;
     const bool active = (i < g.nx) && (j < g.ny);
@@ -129,11 +133,13 @@ k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict_
             jy = ky.value();
             en = ke.value();
         }
-        const double ux = jx / n, uy = jy / n;
-        const double T = 0.5 * (en / n - ux * ux - uy * uy);
+        const double inv_n = recip_nr(n);
+        const double ux = jx * inv_n, uy = jy * inv_n;
+        const double T = 0.5 * (en * inv_n - ux * ux - uy * uy);
         // Delta p = n T - p^w, p^w = n T / (1 - b n) - a n^2 (Eq. vdw)
+        const double nT = n * T;
         sm.n[r][c] = (real)n;
-        sm.dp[r][c] = (real)(n * T - (n * T / (1.0 - g.b * n) - g.a * n * n));
+        sm.dp[r][c] = (real)(nT - fma(nT, recip_nr(1.0 - g.b * n), -g.a * n * n));
         const int tr = r - 3, tc = c - 4;
         if (tr >= 0 && tr < TY && tc >= 0 && tc < TX) {
             sm.ux[tr][tc] = (real)ux;
@@ -228,9 +234,8 @@ k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict_
     }
     __syncthreads();
 
-    // ---- 4. force and equilibrium factors at the tile node
-    real Fx = 0, Fy = 0, nn = 1, gx[NQ], gy[NQ];
-    if (active) {
+    // ---- 4. force and equilibrium factors at the tile nodes (lane 0)
+    if (active && lane_k == 0) {
         real ddx = 0, ddy = 0, ldx = 0, ldy = 0;
         constexpr int cy = 3, cx = 4;
 #pragma unroll
@@ -249,47 +254,62 @@ k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict_
                     ldy += w * (sm.n[ty + cy + l][tx + cx + m] - sm.n[ty + cy - l][tx + cx + m]);
                 }
             }
-        nn = sm.n[ty + cy][tx + cx];
-        Fx = ddx * real(g.inv_ds) / nn + real(g.sigma) * ldx * real(g.inv_ds3);
-        Fy = ddy * real(g.inv_ds) / nn + real(g.sigma) * ldy * real(g.inv_ds3);
-        eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], gx);
-        eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gy);
+        const real nn = sm.n[ty + cy][tx + cx];
+        const real dn = real(g.inv_ds) / nn;
+        sm.loc[0][node] = ddx * dn + real(g.sigma) * ldx * real(g.inv_ds3);
+        sm.loc[1][node] = ddy * dn + real(g.sigma) * ldy * real(g.inv_ds3);
+        sm.loc[2][node] = nn;
+        real gq[NQ];
+        eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], gq);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sm.loc[3 + q][node] = gq[q];
+        eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gq);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sm.loc[3 + NQ + q][node] = gq[q];
     }
 
-    // ---- 5. advection, collision and RK combination, one velocity at a time
+    // ---- 5. advection, collision and RK combination, KP velocities at a time
     const int nfx = (TX + 1) * TY, nfy = TX * (TY + 1);
     const long long o = (long long)j * g.pitch + i;
     const real itau = real(g.inv_tau);
     const real cadv = cc * real(g.inv_ds);
-    for (int k = 0; k < NK; ++k) {
-        const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
-        const int nx_faces = (k1 == 2) ? 0 : nfx;
-        const int ny_faces = (k2 == 2) ? 0 : nfy;
-        if (k > 0) __syncthreads();  // the previous velocity's faces are consumed
-        for (int e = tid; e < nx_faces + ny_faces; e += NT) {
-            if (e < nx_faces) {
-                const int r = e / (TX + 1), c = e - r * (TX + 1);
+    for (int kb = 0; kb < NK; kb += KP) {
+        __syncthreads();  // loc ready / the previous velocities' faces are consumed
+        // faces of the KP velocities kb .. kb+KP-1: x faces of the tile rows,
+        // then y faces of the tile columns, each computed once
+        for (int e = tid; e < KP * (nfx + nfy); e += NT) {
+            const int sub = e / (nfx + nfy), f = e - sub * (nfx + nfy);
+            const int k = kb + sub;
+            if (k >= NK) continue;
+            const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
+            if (f < nfx) {
+                if (k1 == 2) continue;
+                const int r = f / (TX + 1), c = f - r * (TX + 1);
                 if (y0 + r < g.ny && x0 + c <= g.nx) {
                     // face at x = x0 + c: nodes x0+c-3 .. x0+c+2 are columns c+1 .. c+6
                     const real *row = &sm.pop[k][3 + r][0];
-                    sm.fx[r][c] = (k1 > 2) ? weno5(row[c + 1], row[c + 2], row[c + 3], row[c + 4], row[c + 5])
-                                           : weno5(row[c + 6], row[c + 5], row[c + 4], row[c + 3], row[c + 2]);
+                    sm.fx[sub][r][c] = (k1 > 2) ? weno5(row[c + 1], row[c + 2], row[c + 3], row[c + 4], row[c + 5])
+                                                : weno5(row[c + 6], row[c + 5], row[c + 4], row[c + 3], row[c + 2]);
                 }
             } else {
-                const int e2 = e - nx_faces;
+                if (k2 == 2) continue;
+                const int e2 = f - nfx;
                 const int r = e2 / TX, c = e2 - r * TX;
                 if (x0 + c < g.nx && y0 + r <= g.ny) {
                     // face at y = y0 + r: rows y0+r-3 .. y0+r+2 are rows r .. r+5
                     const int cc4 = 4 + c;
                     const real(*P)[HX] = sm.pop[k];
-                    sm.fy[r][c] = (k2 > 2) ? weno5(P[r][cc4], P[r + 1][cc4], P[r + 2][cc4], P[r + 3][cc4], P[r + 4][cc4])
-                                           : weno5(P[r + 5][cc4], P[r + 4][cc4], P[r + 3][cc4], P[r + 2][cc4],
-                                                   P[r + 1][cc4]);
+                    sm.fy[sub][r][c] = (k2 > 2) ? weno5(P[r][cc4], P[r + 1][cc4], P[r + 2][cc4], P[r + 3][cc4],
+                                                        P[r + 4][cc4])
+                                                : weno5(P[r + 5][cc4], P[r + 4][cc4], P[r + 3][cc4], P[r + 2][cc4],
+                                                        P[r + 1][cc4]);
                 }
             }
         }
         __syncthreads();
-        if (active) {
+        const int k = kb + lane_k;
+        if (active && k < NK) {
+            const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
             const int r = ty + 3, c = tx + 4;
             real dx = 0, dy = 0;
 #pragma unroll
@@ -298,11 +318,11 @@ k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict_
                 dy += t.D[k2][q] * sm.pop[NQ * k1 + q][r][c];
             }
             const real f = sm.pop[k][r][c];
-            const real feq = nn * sel5(gx, k1) * sel5(gy, k2);
+            const real feq = sm.loc[2][node] * sm.loc[3 + k1][node] * sm.loc[3 + NQ + k2][node];
             real adv = 0;
-            if (k1 != 2) adv += t.R[k1] * (sm.fx[ty][tx + 1] - sm.fx[ty][tx]);
-            if (k2 != 2) adv += t.R[k2] * (sm.fy[ty + 1][tx] - sm.fy[ty][tx]);
-            const real Lloc = -(Fx * dx + Fy * dy) - (f - feq) * itau;
+            if (k1 != 2) adv += t.R[k1] * (sm.fx[lane_k][ty][tx + 1] - sm.fx[lane_k][ty][tx]);
+            if (k2 != 2) adv += t.R[k2] * (sm.fy[lane_k][ty + 1][tx] - sm.fy[lane_k][ty][tx]);
+            const real Lloc = -(sm.loc[0][node] * dx + sm.loc[1][node] * dy) - (f - feq) * itau;
             real v = cb * f + cc * Lloc - cadv * adv;
             if (ca != real(0)) v += ca * fn[k * g.plane + o];
             out[k * g.plane + o] = v;
@@ -310,39 +330,39 @@ k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict_
     }
 }
 
-// Tile shapes compiled for each precision; the context picks one per grid.
-template <typename real, int TX, int TY>
+template <typename real, int TX, int TY, int KP>
 cudaError_t fused_prepare_one()
 {
-    return cudaFuncSetAttribute(k_fused<real, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(FusedSmem<real, TX, TY>));
+    return cudaFuncSetAttribute(k_fused<real, TX, TY, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(FusedSmem<real, TX, TY, KP>));
 }
 
-template <typename real, int TX, int TY>
+template <typename real, int TX, int TY, int KP>
 cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *status, const Geo &g,
                              const Tab<real> &t, StageCoef c, cudaStream_t s)
 {
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-    k_fused<real, TX, TY><<<grid, TX * TY, sizeof(FusedSmem<real, TX, TY>), s>>>(
+    k_fused<real, TX, TY, KP><<<grid, TX * TY * KP, sizeof(FusedSmem<real, TX, TY, KP>), s>>>(
         fs, fn, out, status, g, t, (real)c.ca, (real)c.cb, (real)c.cc);
     return cudaGetLastError();
 }
 
-// Tile shapes compiled for each precision (TX x TY nodes per CTA); the
-// context picks one per grid (olb_set_tile overrides).
-#define OLB_FUSED_SHAPE_CASES(real, DO) DO(real, 8, 8) DO(real, 16, 8) DO(real, 32, 8) DO(real, 32, 16)
-#define OLB_FUSED_PREP_CASE(real, A, B) \
-    if (tx == A && ty == B) return fused_prepare_one<real, A, B>();
-#define OLB_FUSED_LAUNCH_CASE(real, A, B) \
-    if (tx == A && ty == B) return fused_launch_one<real, A, B>(fs, fn, out, status, g, t, c, s);
+// Shapes compiled for each precision: TX x TY nodes per CTA, KP velocities
+// advanced at once (TX*TY*KP threads).  Must match TILE_X/TILE_Y/TILE_K in
+// olb_internal.cuh.
+#define OLB_FUSED_SHAPE_CASES(real, DO) DO(real, 8, 8, 4) DO(real, 16, 8, 2) DO(real, 16, 8, 1) DO(real, 32, 8, 1) DO(real, 32, 16, 1)
+#define OLB_FUSED_PREP_CASE(real, A, B, C) \
+    if (tx == A && ty == B && kp == C) return fused_prepare_one<real, A, B, C>();
+#define OLB_FUSED_LAUNCH_CASE(real, A, B, C) \
+    if (tx == A && ty == B && kp == C) return fused_launch_one<real, A, B, C>(fs, fn, out, status, g, t, c, s);
 #define OLB_DEFINE_FUSED(real)                                                                                \
-    cudaError_t prepare_fused(real *, int tx, int ty)                                                         \
+    cudaError_t prepare_fused(real *, int tx, int ty, int kp)                                                 \
     {                                                                                                         \
         OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_PREP_CASE)                                                      \
         return cudaErrorInvalidValue;                                                                         \
     }                                                                                                         \
     cudaError_t launch_fused(const real *fs, const real *fn, real *out, int *status, const Geo &g,            \
-                             const Tab<real> &t, StageCoef c, int tx, int ty, cudaStream_t s)                 \
+                             const Tab<real> &t, StageCoef c, int tx, int ty, int kp, cudaStream_t s)         \
     {                                                                                                         \
         OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_LAUNCH_CASE)                                                    \
         return cudaErrorInvalidValue;                                                                         \

@@ -54,9 +54,9 @@ struct StageCoef {
 // Launchers, one set per precision (olb_fp64.cu, olb_fp32.cu).  Output
 // pointers of launch_moments_out may be NULL to skip a field.
 #define OLB_DECLARE_LAUNCHERS(real)                                                                    \
-    cudaError_t prepare_fused(real *, int tx, int ty);                                                 \
+    cudaError_t prepare_fused(real *, int tx, int ty, int kp);                                         \
     cudaError_t launch_fused(const real *fs, const real *fn, real *out, int *status, const Geo &g,     \
-                             const Tab<real> &t, StageCoef c, int tx, int ty, cudaStream_t s);         \
+                             const Tab<real> &t, StageCoef c, int tx, int ty, int kp, cudaStream_t s); \
     cudaError_t launch_init(real *f, const double *n, const double *ux, const double *uy,              \
                             const double *T, const Geo &g, const Tab<real> &t, cudaStream_t s);         \
     cudaError_t launch_moments_out(const real *f, double *n, double *ux, double *uy, double *T,        \
@@ -67,9 +67,11 @@ struct StageCoef {
 OLB_DECLARE_LAUNCHERS(double)
 OLB_DECLARE_LAUNCHERS(float)
 
-// Stage-kernel tile shapes compiled for both precisions.
-constexpr int NUM_TILES = 4;
-constexpr int TILE_X[NUM_TILES] = {8, 16, 32, 32};
-constexpr int TILE_Y[NUM_TILES] = {8, 8, 8, 16};
+// Stage-kernel shapes compiled for both precisions: TX x TY nodes per CTA
+// and KP velocities advanced at once, listed by increasing tile area.
+constexpr int NUM_TILES = 5;
+constexpr int TILE_X[NUM_TILES] = {8, 16, 16, 32, 32};
+constexpr int TILE_Y[NUM_TILES] = {8, 8, 8, 8, 16};
+constexpr int TILE_K[NUM_TILES] = {4, 2, 1, 1, 1};
 
 }  // namespace olb

@@ -40,31 +40,54 @@ __host__ __device__ constexpr double glap_c(int am, int l)
 }
 
 // ---------------------------------------------------------------- WENO-5
+// Reciprocal of d > 0 in FP64: the hardware approximation rcp.approx.ftz.f64
+// as a seed, refined by two Newton-Raphson steps r <- r (2 - d r) (each
+// doubles the number of correct bits), written as fused multiply-adds.
+// Flushes subnormal d to zero (d < 2.2e-308 gives +inf).
+__device__ __forceinline__ double recip_nr(double d)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
 // v0..v4 = f_{i-2} .. f_{i+2} in the upwind orientation; returns the WENO-5
 // interface value sum_q wbar_q Fhat^q (without p/m).
 //
+// In terms of the first differences d01 = v1 - v0, ..., d34 = v4 - v3:
+//   sigma_q = 13/12 a_q^2 + 1/4 b_q^2 with a_1 = d12 - d01, b_1 = 3 d12 - d01,
+//   a_2 = d23 - d12, b_2 = d12 + d23, a_3 = d34 - d23, b_3 = d34 - 3 d23
+//   (Eq. weno5_sigma), and Fhat^q = v2 + G_q with G_1 = (5 d12 - 2 d01)/6,
+//   G_2 = (d12 + 2 d23)/6, G_3 = (4 d23 - d34)/6 (the candidates of
+//   Eq. weno5_flux).  The weights only depend on ratios of the sigma_q, so
+//   12 sigma_q = 13 a_q^2 + 3 b_q^2 is used.
+//
 // Weights: wbar_q is proportional to delta_q / sigma_q^2.  Multiplying every
-// term by sigma_1^2 sigma_2^2 sigma_3^2 gives weights proportional to
-// A_q = delta_q prod_{r != q} sigma_r^2, which needs one division, equals the
-// table row for a single vanishing indicator, and is 0/0 only when two or
-// three vanish; those cases take Table tab:weno (the ideal weights of the
+// term by (sigma_1 sigma_2 sigma_3)^2 gives weights proportional to
+// A_q = delta_q (prod_{r != q} sigma_r)^2, which needs one reciprocal, equals
+// the table row for a single vanishing indicator, and is 0/0 only when two
+// or three vanish; those cases take Table tab:weno (the ideal weights of the
 // vanishing set).  If the products underflow without an exact zero the
 // min-scaled form delta_q (s/sigma_q)^2 is used instead.
 __device__ __forceinline__ double weno5(double v0, double v1, double v2, double v3, double v4)
 {
-    const double a1 = v0 - 2.0 * v1 + v2, b1 = v0 - 4.0 * v1 + 3.0 * v2;
-    const double a2 = v1 - 2.0 * v2 + v3, b2 = v1 - v3;
-    const double a3 = v2 - 2.0 * v3 + v4, b3 = 3.0 * v2 - 4.0 * v3 + v4;
-    const double s1 = (13.0 / 12.0) * a1 * a1 + 0.25 * b1 * b1;
-    const double s2 = (13.0 / 12.0) * a2 * a2 + 0.25 * b2 * b2;
-    const double s3 = (13.0 / 12.0) * a3 * a3 + 0.25 * b3 * b3;
-    const double F1 = (1.0 / 3.0) * v0 - (7.0 / 6.0) * v1 + (11.0 / 6.0) * v2;
-    const double F2 = (-1.0 / 6.0) * v1 + (5.0 / 6.0) * v2 + (1.0 / 3.0) * v3;
-    const double F3 = (1.0 / 3.0) * v2 + (5.0 / 6.0) * v3 - (1.0 / 6.0) * v4;
-    const double q1 = s1 * s1, q2 = s2 * s2, q3 = s3 * s3;
-    const double A1 = 0.1 * (q2 * q3), A2 = 0.6 * (q1 * q3), A3 = 0.3 * (q1 * q2);
+    const double d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
+    const double a1 = d12 - d01, b1 = fma(3.0, d12, -d01);
+    const double a2 = d23 - d12, b2 = d12 + d23;
+    const double a3 = d34 - d23, b3 = fma(-3.0, d23, d34);
+    const double s1 = fma(13.0 * a1, a1, 3.0 * b1 * b1);
+    const double s2 = fma(13.0 * a2, a2, 3.0 * b2 * b2);
+    const double s3 = fma(13.0 * a3, a3, 3.0 * b3 * b3);
+    const double G1 = fma(5.0 / 6.0, d12, (-1.0 / 3.0) * d01);
+    const double G2 = fma(1.0 / 3.0, d23, (1.0 / 6.0) * d12);
+    const double G3 = fma(2.0 / 3.0, d23, (-1.0 / 6.0) * d34);
+    const double p1 = s2 * s3, p2 = s1 * s3, p3 = s1 * s2;
+    const double A1 = (0.1 * p1) * p1, A2 = (0.6 * p2) * p2, A3 = (0.3 * p3) * p3;
     const double den = A1 + A2 + A3;
-    if (den > 0.0) return (A1 * F1 + A2 * F2 + A3 * F3) / den;
+    if (den > 2.3e-308) return fma(fma(A1, G1, fma(A2, G2, A3 * G3)), recip_nr(den), v2);
     double w1, w2, w3;
     if (s1 == 0.0 || s2 == 0.0 || s3 == 0.0) {
         w1 = (s1 == 0.0) ? 0.1 : 0.0;
@@ -77,23 +100,25 @@ __device__ __forceinline__ double weno5(double v0, double v1, double v2, double 
         w2 = 0.6 * r2 * r2;
         w3 = 0.3 * r3 * r3;
     }
-    return (w1 * F1 + w2 * F2 + w3 * F3) / (w1 + w2 + w3);
+    return v2 + (w1 * G1 + w2 * G2 + w3 * G3) / (w1 + w2 + w3);
 }
 
-// FP32 form: the products of four squared indicators underflow in single
-// precision, so the weights are always the min-scaled delta_q (s/sigma_q)^2
-// (same normalised weights), with Table tab:weno when an indicator vanishes.
+// FP32 form (same differences): the products of four squared indicators
+// underflow in single precision, so the weights are always the min-scaled
+// delta_q (s/sigma_q)^2 (same normalised weights), with Table tab:weno when
+// an indicator vanishes.
 __device__ __forceinline__ float weno5(float v0, float v1, float v2, float v3, float v4)
 {
-    const float a1 = v0 - 2.0f * v1 + v2, b1 = v0 - 4.0f * v1 + 3.0f * v2;
-    const float a2 = v1 - 2.0f * v2 + v3, b2 = v1 - v3;
-    const float a3 = v2 - 2.0f * v3 + v4, b3 = 3.0f * v2 - 4.0f * v3 + v4;
-    const float s1 = (13.0f / 12.0f) * a1 * a1 + 0.25f * b1 * b1;
-    const float s2 = (13.0f / 12.0f) * a2 * a2 + 0.25f * b2 * b2;
-    const float s3 = (13.0f / 12.0f) * a3 * a3 + 0.25f * b3 * b3;
-    const float F1 = (1.0f / 3.0f) * v0 - (7.0f / 6.0f) * v1 + (11.0f / 6.0f) * v2;
-    const float F2 = (-1.0f / 6.0f) * v1 + (5.0f / 6.0f) * v2 + (1.0f / 3.0f) * v3;
-    const float F3 = (1.0f / 3.0f) * v2 + (5.0f / 6.0f) * v3 - (1.0f / 6.0f) * v4;
+    const float d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
+    const float a1 = d12 - d01, b1 = fmaf(3.0f, d12, -d01);
+    const float a2 = d23 - d12, b2 = d12 + d23;
+    const float a3 = d34 - d23, b3 = fmaf(-3.0f, d23, d34);
+    const float s1 = fmaf(13.0f * a1, a1, 3.0f * b1 * b1);
+    const float s2 = fmaf(13.0f * a2, a2, 3.0f * b2 * b2);
+    const float s3 = fmaf(13.0f * a3, a3, 3.0f * b3 * b3);
+    const float G1 = fmaf(5.0f / 6.0f, d12, (-1.0f / 3.0f) * d01);
+    const float G2 = fmaf(1.0f / 3.0f, d23, (1.0f / 6.0f) * d12);
+    const float G3 = fmaf(2.0f / 3.0f, d23, (-1.0f / 6.0f) * d34);
     float w1, w2, w3;
     const float s = fminf(s1, fminf(s2, s3));
     if (s > 0.0f) {
@@ -106,7 +131,7 @@ __device__ __forceinline__ float weno5(float v0, float v1, float v2, float v3, f
         w2 = (s2 == 0.0f) ? 0.6f : 0.0f;
         w3 = (s3 == 0.0f) ? 0.3f : 0.0f;
     }
-    return __fdividef(w1 * F1 + w2 * F2 + w3 * F3, w1 + w2 + w3);
+    return fmaf(fmaf(w1, G1, fmaf(w2, G2, w3 * G3)), __fdividef(1.0f, w1 + w2 + w3), v2);
 }
 
 // ---------------------------------------------------------------- helpers

@@ -65,9 +65,9 @@ for _n in ("olb_get_populations", "olb_set_populations"):
     getattr(_lib, _n).argtypes = [_VP, _VP]
     getattr(_lib, _n).restype = ctypes.c_int
 _lib.olb_profile.argtypes = [_VP, ctypes.c_int, _VP, _VP]
-_lib.olb_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+_lib.olb_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
 _lib.olb_set_tile.restype = ctypes.c_int
-_lib.olb_get_tile.argtypes = [_VP, _VP, _VP]
+_lib.olb_get_tile.argtypes = [_VP, _VP, _VP, _VP]
 _lib.olb_get_tile.restype = ctypes.c_int
 _lib.olb_profile.restype = ctypes.c_int
 _lib.olb_status_string.argtypes = [ctypes.c_int]
@@ -224,14 +224,13 @@ class Context:
                "olb_profile")
         return {"stage_ms": float(ms[0]), "stage_launches": int(cnt[0])}
 
-    def set_tile(self, tx: int, ty: int) -> None:
-        _check(_lib.olb_set_tile(self._h, int(tx), int(ty)), "olb_set_tile")
+    def set_tile(self, tx: int, ty: int, kp: int) -> None:
+        _check(_lib.olb_set_tile(self._h, int(tx), int(ty), int(kp)), "olb_set_tile")
 
     def get_tile(self):
-        a = ctypes.c_int()
-        b = ctypes.c_int()
-        _check(_lib.olb_get_tile(self._h, ctypes.byref(a), ctypes.byref(b)), "olb_get_tile")
-        return a.value, b.value
+        v = [ctypes.c_int() for _ in range(3)]
+        _check(_lib.olb_get_tile(self._h, *[ctypes.byref(x) for x in v]), "olb_get_tile")
+        return tuple(x.value for x in v)
 
     def get_populations(self) -> np.ndarray:
         out = np.zeros((25, self.ny, self.nx))

@@ -286,3 +286,29 @@ def test_planar_workload_long_run_conserves_mass(olb):
     assert abs(m[0].sum() - m0.sum()) < 1e-12 * m0.sum()
     assert np.all(np.isfinite(m[3])) and m[3].min() > 0.85
     assert m[0][:, :8].mean() > m0[:, :8].mean()
+
+
+@pytest.mark.parametrize("side_x", [0, 1])
+def test_every_tile_shape_gives_identical_results(olb, side_x):
+    """The stage kernel's shapes (tile size, velocity lanes) only change which
+    thread computes what: populations agree bit for bit."""
+    p = inputs.RunParams(nx=45, ny=19, ds=1.0 / 45, dt=0.2 / 45 / inputs.P_MAX, tau=0.01,
+                         Tw=(0.85, 0.95), side_x=side_x)
+    fl = noisy(p, seed=9, amp=0.05, uamp=0.01)
+    ref = None
+    for shape in ((8, 8, 4), (16, 8, 2), (16, 8, 1), (32, 8, 1), (32, 16, 1)):
+        ctx = olb.create(p)
+        ctx.set_tile(*shape)
+        assert ctx.get_tile() == shape
+        ctx.init_fields(*fl)
+        ctx.step(4)
+        f = ctx.get_populations()
+        if ref is None:
+            ref = f
+            o = make_oracle(p, fl)
+            o.step(4)
+            assert field_rel(f, o.get_populations()) < FP64_TOL
+        else:
+            assert np.array_equal(f, ref), shape
+    with pytest.raises(olb.OlbError):
+        ctx.set_tile(8, 8, 1)
