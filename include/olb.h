@@ -171,9 +171,11 @@ int olb_profile(olb_ctx *ctx, int nsteps, double *ms, int *launches);
 
 /* Shape of the stage kernel: tx x ty nodes per CTA, kp velocities advanced
  * at once (tx*ty*kp threads).  Compiled shapes (tx, ty, kp): (8,8,4),
- * (16,8,2), (16,8,1), (32,8,1), (32,16,1); olb_create picks one from the
- * grid size.  olb_set_tile returns OLB_ERR_ARG for any other shape; results
- * do not depend on the shape.  Not part of the paper (a tuning knob). */
+ * (16,8,2), (16,8,1), (32,8,1), (32,16,1) -- the last only for
+ * OLB_FP32_KAHAN (its FP64 tile exceeds the shared memory of a CTA);
+ * olb_create picks one from the grid size.  olb_set_tile returns
+ * OLB_ERR_ARG for any other shape; results do not depend on the shape.
+ * Not part of the paper (a tuning knob). */
 int olb_set_tile(olb_ctx *ctx, int tx, int ty, int kp);
 int olb_get_tile(olb_ctx *ctx, int *tx, int *ty, int *kp);
 

@@ -603,11 +603,12 @@ extern "C" int olb_set_tile(olb_ctx *c, int tx, int ty, int kp)
     c->kp = kp;
     e = prepare_tile(c);
     if (e != cudaSuccess) {
+        // a shape whose shared memory exceeds the per-CTA limit is refused
         c->tx = otx;
         c->ty = oty;
         c->kp = okp;
         cudaGetLastError();
-        return cuda_status(e);
+        return e == cudaErrorInvalidValue ? OLB_ERR_ARG : cuda_status(e);
     }
     drop_graphs(c);
     return OLB_OK;

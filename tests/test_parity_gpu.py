@@ -195,14 +195,18 @@ def window_check(olb, p, fields, windows, margin=10, steps=1):
     """One GPU run at full size; the oracle on windows around sample points.
     A node depends on nodes at most 3 away per stage (WENO stencil and the
     49-point stencils of pointwise moments), 9 per RK-3 step, so the window
-    interior more than 9*steps from a cut edge is exact.  Each field must lie
-    within max(1e-11 x its magnitude over the whole grid, 10 x the rounding
-    envelope of the window).  Returns the worst error / allowed ratio and
-    per-window, per-field details."""
+    interior more than 9*steps from a cut edge is exact.  The populations and
+    n, T must agree within 1e-11 of their magnitude over the whole grid; u,
+    which one step only just creates and which is a small difference of O(1)
+    populations, within max(1e-11 x |u|max, 100 x the rounding envelope of
+    the window).  Returns the worst error / allowed ratio and per-window,
+    per-field details."""
     ctx = olb.create(p)
     ctx.init_fields(*fields)
     assert ctx.step(steps) == 0
     m_gpu = ctx.moments()
+    f_gpu = ctx.get_populations()
+    fscale = np.max(np.abs(f_gpu))
     us = max(np.max(np.abs(m_gpu[1])), np.max(np.abs(m_gpu[2])))
     scale = [np.max(np.abs(m_gpu[0])), us, us, np.max(np.abs(m_gpu[3]))]
     worst = 0.0
@@ -214,6 +218,7 @@ def window_check(olb, p, fields, windows, margin=10, steps=1):
         sub = crop_window(fields, x0, y0, wx, wy, p.nx, p.ny, p.side_x == 0)
         env, o = rounding_envelope(wp, sub, steps)
         mo = o.moments()
+        fo = o.get_populations()
         inner_y = slice(margin * steps, wy - margin * steps)
         if at_wall == "left":
             inner_x = slice(0, wx - margin * steps)
@@ -223,11 +228,18 @@ def window_check(olb, p, fields, windows, margin=10, steps=1):
             inner_x = slice(margin * steps, wx - margin * steps)
         ys = np.arange(y0, y0 + wy) % p.ny
         xs = np.arange(x0, x0 + wx) % p.nx
+        fg = f_gpu[:, ys][:, :, xs][:, inner_y, inner_x]
+        ratio_f = float(np.max(np.abs(fg - fo[:, inner_y, inner_x])) / (FP64_TOL * fscale))
+        details.append(dict(window=(x0, y0), field="f", ratio=ratio_f, gpu=0.0, oracle=0.0, env=0.0,
+                            scale=float(fscale), at=(0, 0)))
+        worst = max(worst, ratio_f)
         for k in range(4):
             g = m_gpu[k][np.ix_(ys, xs)][inner_y, inner_x]
             r = mo[k][inner_y, inner_x]
             e = env[k][inner_y, inner_x]
-            allowed = np.maximum(FP64_TOL * scale[k], 10.0 * e)
+            allowed = np.full(g.shape, FP64_TOL * scale[k])
+            if k in (1, 2):
+                allowed = np.maximum(allowed, 100.0 * e)
             ratio = np.abs(g - r) / allowed
             q = np.unravel_index(np.argmax(ratio), ratio.shape)
             details.append(dict(window=(x0, y0), field="n ux uy T".split()[k], ratio=float(ratio[q]),
@@ -237,6 +249,11 @@ def window_check(olb, p, fields, windows, margin=10, steps=1):
     return worst, details
 
 
+def fmt_detail(d):
+    return (f"window {d['window']} {d['field']} at {d['at']}: ratio {d['ratio']:.3g} gpu {d['gpu']:.17g} "
+            f"oracle {d['oracle']:.17g} envelope {d['env']:.3g} scale {d['scale']:.3g}")
+
+
 def test_laplace_2048_sampled_windows(olb):
     """Laplace-drop workload at full size (2048^2 periodic) after one step,
     sampled on oracle windows across the drop interface and in the bulk."""
@@ -244,7 +261,7 @@ def test_laplace_2048_sampled_windows(olb):
     wins = [(1024 - 20 + dx, 1024 + 410 - 20 + dy, 40, 40, None) for dx, dy in ((0, 0), (300, -100))]
     wins += [(2048 - 20, 2048 - 20, 40, 40, None)]  # wraps both axes
     worst, details = window_check(olb, p, fl, wins)
-    assert worst < 1.0, [d for d in details if d["ratio"] > 0.3]
+    assert worst < 1.0, "; ".join(fmt_detail(d) for d in details if d["ratio"] > 0.3)
 
 
 def test_phase_separation_4096_sampled_windows(olb):
@@ -253,7 +270,7 @@ def test_phase_separation_4096_sampled_windows(olb):
     p, fl = inputs.phase_separation(4096, steps=1)
     wins = [(0, 100, 40, 40, "left"), (4096 - 40, 3000, 40, 40, "right"), (2000, 4096 - 20, 40, 40, None)]
     worst, details = window_check(olb, p, fl, wins)
-    assert worst < 1.0, [d for d in details if d["ratio"] > 0.3]
+    assert worst < 1.0, "; ".join(fmt_detail(d) for d in details if d["ratio"] > 0.3)
 
 
 # ------------------------------------------------------------------ FP32 + Kahan
@@ -296,7 +313,7 @@ def test_every_tile_shape_gives_identical_results(olb, side_x):
                          Tw=(0.85, 0.95), side_x=side_x)
     fl = noisy(p, seed=9, amp=0.05, uamp=0.01)
     ref = None
-    for shape in ((8, 8, 4), (16, 8, 2), (16, 8, 1), (32, 8, 1), (32, 16, 1)):
+    for shape in ((8, 8, 4), (16, 8, 2), (16, 8, 1), (32, 8, 1)):
         ctx = olb.create(p)
         ctx.set_tile(*shape)
         assert ctx.get_tile() == shape
@@ -312,3 +329,7 @@ def test_every_tile_shape_gives_identical_results(olb, side_x):
             assert np.array_equal(f, ref), shape
     with pytest.raises(olb.OlbError):
         ctx.set_tile(8, 8, 1)
+    with pytest.raises(olb.OlbError):  # FP64 32 x 16 does not fit in shared memory
+        ctx.set_tile(32, 16, 1)
+    c32 = olb.create(p, olb.FP32_KAHAN)
+    c32.set_tile(32, 16, 1)
