@@ -50,7 +50,7 @@ def make_oracle(p, fields):
 EPS = float(np.finfo(np.float64).eps)
 
 
-def rounding_envelope(p, fields, steps, ulps=64.0, seed=0):
+def rounding_envelope(p, fields, steps, ulps=4.0, seed=0):
     """How far two correct FP64 evaluations of the same run can drift apart.
 
     The step is ill-conditioned where the 49-point stencils of Eq. F_def
@@ -58,12 +58,10 @@ def rounding_envelope(p, fields, steps, ulps=64.0, seed=0):
     change of the state moves the force by up to ~1e6 ulp.  The oracle is run
     twice, the second time with every population multiplied by
     1 + ulps * eps * U(-1, 1) before each step, a stand-in for the rounding
-    of one RK-3 step done in another order: summing a 49-tap stencil in
-    another order moves it by up to ~49 roundings of its largest terms, and
-    a random perturbation of 64 ulp per population moves the moments (sums
-    of 25 populations) and hence the stencil sums by about as much.  The
-    absolute differences of (n, u_x, u_y, T) between the two runs and the
-    unperturbed oracle are returned."""
+    of one RK-3 step done in another order.  The absolute differences of
+    (n, u_x, u_y, T) between the two runs and the unperturbed oracle are
+    returned; callers bound errors by the maximum of a difference over the
+    compared region (pointwise, a random perturbation can happen to cancel)."""
     a = make_oracle(p, fields)
     b = make_oracle(p, fields)
     rng = np.random.default_rng(seed)
@@ -77,14 +75,14 @@ def rounding_envelope(p, fields, steps, ulps=64.0, seed=0):
 
 def check_against_envelope(m_gpu, p, fields, steps, rtol=1e-11, factor=10.0):
     """GPU moments vs the oracle: each field within max(rtol x its magnitude,
-    factor x the rounding envelope), elementwise.  Returns the worst ratio
-    error / allowed (< 1 passes) per field."""
+    factor x the largest spread of the rounding envelope over the grid).
+    Returns the worst ratio error / allowed (< 1 passes) per field."""
     env, o = rounding_envelope(p, fields, steps)
     ref = o.moments()
     us = max(np.max(np.abs(ref[1])), np.max(np.abs(ref[2])), 1e-300)
     scales = [np.max(np.abs(ref[0])), us, us, np.max(np.abs(ref[3]))]
     out = {}
     for name, g, r, e, s in zip(("n", "ux", "uy", "T"), m_gpu, ref, env, scales):
-        allowed = np.maximum(rtol * s, factor * e)
+        allowed = max(rtol * s, factor * float(np.max(e)))
         out[name] = float(np.max(np.abs(np.asarray(g) - r) / allowed))
     return out
