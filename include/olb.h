@@ -179,6 +179,35 @@ int olb_profile(olb_ctx *ctx, int nsteps, double *ms, int *launches);
 int olb_set_tile(olb_ctx *ctx, int tx, int ty, int kp);
 int olb_get_tile(olb_ctx *ctx, int *tx, int *ty, int *kp);
 
+/* Largest grid (nx * ny nodes) olb_step_static accepts. */
+#define OLB_STATIC_MAX_NODES 16384
+
+/* Whole FP64 RK-3 steps without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that must not call
+ * cudaMalloc / cudaFree when they step a small grid -- those calls
+ * synchronise the whole device and stall every other stream, and some host
+ * applications give all device memory to their own pool up front or load
+ * the library as a plug-in that may not touch the allocator.
+ *
+ * f: caller-owned device array of the populations, FP64 [25][ny][nx] in the
+ * exchange layout of olb_get_populations, read and overwritten in place with
+ * the state after nsteps >= 0 steps; *p as for olb_create, with precision
+ * OLB_FP64 and at most OLB_STATIC_MAX_NODES nodes (larger grids and other
+ * precisions return OLB_ERR_ARG before any device work; invalid physics
+ * returns OLB_ERR_CFL like olb_create).  The work runs on `stream` (a
+ * cudaStream_t or NULL) and the call returns after it has completed, with
+ * OLB_ERR_DIVERGED if an invalid moment was met, else OLB_OK.
+ *
+ * The two intermediate RK-3 buffers and the status word live in one
+ * file-scope device array of 2 * 25 * OLB_STATIC_MAX_NODES doubles (6.6 MB)
+ * that every GPU which loads the library keeps until the process exits.  The
+ * first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents (the status
+ * word is cleared by each call): calls that overlap on the GPU -- on two
+ * streams, or from two threads -- race and give wrong results. */
+int olb_step_static(const olb_params *p, void *stream, double *f, int nsteps);
+
 /* Human-readable name of a status code (static string). */
 const char *olb_status_string(int status);
 

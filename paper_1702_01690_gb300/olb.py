@@ -29,7 +29,7 @@ WENO_JS = 0
 SYMBOLS = ("olb_set_allocator", "olb_create", "olb_destroy", "olb_init_fields",
            "olb_init_fields_device", "olb_step", "olb_step_async", "olb_get_status",
            "olb_moments", "olb_moments_device", "olb_get_populations",
-           "olb_set_populations", "olb_status_string", "olb_profile", "olb_set_tile", "olb_get_tile")
+           "olb_set_populations", "olb_status_string", "olb_profile", "olb_set_tile", "olb_get_tile", "olb_step_static")
 
 
 class Params(ctypes.Structure):
@@ -70,6 +70,9 @@ _lib.olb_set_tile.restype = ctypes.c_int
 _lib.olb_get_tile.argtypes = [_VP, _VP, _VP, _VP]
 _lib.olb_get_tile.restype = ctypes.c_int
 _lib.olb_profile.restype = ctypes.c_int
+_lib.olb_step_static.argtypes = [ctypes.POINTER(Params), _VP, _VP, ctypes.c_int]
+_lib.olb_step_static.restype = ctypes.c_int
+STATIC_MAX_NODES = 16384
 _lib.olb_status_string.argtypes = [ctypes.c_int]
 _lib.olb_status_string.restype = ctypes.c_char_p
 
