@@ -179,6 +179,54 @@ int olb_profile(olb_ctx *ctx, int nsteps, double *ms, int *launches);
 int olb_set_tile(olb_ctx *ctx, int tx, int ty, int kp);
 int olb_get_tile(olb_ctx *ctx, int *tx, int *ty, int *kp);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent runs (uneven grid sizes, each with its own
+ * olb_params) advanced together, one persistent launch per RK-3 stage that
+ * strides over all (run, tile) work items, replayed from CUDA graphs.  Not
+ * part of the paper: it serves parameter sweeps (ds, T_w, drop radius) whose
+ * single grids are too small to fill the GPU.  All runs must share the
+ * precision.  Conventions as for single contexts; `run` indexes the array
+ * given to olb_batch_create.  Device memory is allocated with cudaMalloc.
+ * ------------------------------------------------------------------------ */
+typedef struct olb_batch olb_batch;
+
+/* Validate every run as olb_create does (first failing code returned) and
+ * create the batch on the current device, working on `stream`. */
+int olb_batch_create(const olb_params *runs, int count, void *stream, olb_batch **out);
+void olb_batch_destroy(olb_batch *b);
+
+/* f = f^eq of host fields [ny][nx] for one run (as olb_init_fields). */
+int olb_batch_init_fields(olb_batch *b, int run, const double *n, const double *ux,
+                          const double *uy, const double *T);
+
+/* Advance every run by nsteps RK-3 steps (each with its own dt).  olb_batch_step
+ * synchronises and returns OLB_ERR_DIVERGED if any run diverged;
+ * olb_batch_step_async only enqueues.  All runs must be initialised. */
+int olb_batch_step(olb_batch *b, int nsteps);
+int olb_batch_step_async(olb_batch *b, int nsteps);
+
+/* Synchronise; per_run[r] (if not NULL) receives OLB_OK or OLB_ERR_DIVERGED
+ * per run; returns OLB_ERR_DIVERGED if any run diverged. */
+int olb_batch_get_status(olb_batch *b, int *per_run);
+
+/* Moments / populations of one run into host arrays (as olb_moments,
+ * olb_get_populations). */
+int olb_batch_moments(olb_batch *b, int run, double *n, double *ux, double *uy, double *T);
+int olb_batch_get_populations(olb_batch *b, int run, double *f);
+
+/* Stage-kernel shape of the batch (same compiled shapes as olb_set_tile). */
+int olb_batch_set_tile(olb_batch *b, int tx, int ty, int kp);
+int olb_batch_get_tile(olb_batch *b, int *tx, int *ty, int *kp);
+
+/* Autotuner: times nsteps steps with every compiled shape (on a copy of the
+ * state, which is restored), keeps the fastest and reports it; the choice is
+ * cached per process for the batch's precision, device and grid list. */
+int olb_batch_autotune(olb_batch *b, int nsteps, int *tx, int *ty, int *kp);
+
+/* Mean device time (ms) of one stage launch over nsteps individually
+ * launched steps (the runs advance). */
+int olb_batch_profile(olb_batch *b, int nsteps, double *ms);
+
 /* Largest grid (nx * ny nodes) olb_step_static accepts. */
 #define OLB_STATIC_MAX_NODES 16384
 

@@ -227,7 +227,7 @@ static cudaError_t build_graph(olb_ctx *c, int nsteps, cudaGraphExec_t *exec)
     return e;
 }
 
-static int cuda_status(cudaError_t e)
+int olb::cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return OLB_OK;
     if (e == cudaErrorMemoryAllocation) return OLB_ERR_NOMEM;
@@ -249,7 +249,7 @@ extern "C" const char *olb_status_string(int status)
     }
 }
 
-static int validate(const olb_params *p)
+int olb::validate_params(const olb_params *p)
 {
     if (!p) return OLB_ERR_ARG;
     if (p->nx < 1 || p->ny < 1) return OLB_ERR_ARG;
@@ -298,7 +298,7 @@ extern "C" int olb_create(const olb_params *p, void *stream, olb_ctx **out)
 {
     if (!out) return OLB_ERR_ARG;
     *out = nullptr;
-    int v = validate(p);
+    int v = validate_params(p);
     if (v != OLB_OK) return v;
     olb_ctx *c = new (std::nothrow) olb_ctx();
     if (!c) return OLB_ERR_NOMEM;

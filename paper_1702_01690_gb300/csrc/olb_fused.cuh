@@ -51,21 +51,22 @@ __device__ __forceinline__ real sel5(const real v[NQ], int k)
     return r;
 }
 
+// One stage for the tile whose lower-left node is (x0, y0); all threads of
+// the CTA call it (it synchronises).  g and t may live in parameter space
+// (single grid) or shared memory (batch).
 template <typename real, int TX, int TY, int KP>
-__global__ void __launch_bounds__(TX *TY *KP)
-k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status, Geo g, Tab<real> t,
-        real ca, real cb, real cc)
+__device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, const real *__restrict__ fs,
+                                           const real *fn, real *out, int *__restrict__ status, const Geo &g,
+                                           const Tab<real> &t, const int x0, const int y0, const real ca,
+                                           const real cb, const real cc)
 {
     using S = FusedSmem<real, TX, TY, KP>;
     constexpr int NT = S::NT, NN = S::NN, HX = S::HX, HY = S::HY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    S &sm = *reinterpret_cast<S *>(smem_raw);
 
     // thread = (tile node, velocity lane): KP velocities are advanced at once
     const int tid = threadIdx.x;
     const int node = tid % NN, lane_k = tid / NN;
     const int tx = node % TX, ty = node / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int i = x0 + tx, j = y0 + ty;
     const bool active = (i < g.nx) && (j < g.ny);
 
@@ -330,11 +331,92 @@ k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict_
     }
 }
 
+// Single grid: one CTA per tile.
+template <typename real, int TX, int TY, int KP>
+__global__ void __launch_bounds__(TX *TY *KP)
+k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
+        const __grid_constant__ Geo g, const __grid_constant__ Tab<real> t, real ca, real cb, real cc)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto &sm = *reinterpret_cast<FusedSmem<real, TX, TY, KP> *>(smem_raw);
+    stage_tile<real, TX, TY, KP>(sm, fs, fn, out, status, g, t, blockIdx.x * TX, blockIdx.y * TY, ca, cb, cc);
+}
+
+// Batch of independent runs (uneven grid sizes, own parameters): a
+// persistent grid strides over the (run, tile) work items; tile_start[r] is
+// the first item of run r (prefix sum, tile_start[nruns] = total).  Each run
+// has its populations at offset `off` of the three shared buffers and its own
+// status word.
+template <typename real>
+struct BatchRun {
+    Geo g;
+    Tab<real> t;
+    long long off;
+    int ntx, pad;
+};
+
+template <typename real, int TX, int TY, int KP>
+__global__ void __launch_bounds__(TX *TY *KP)
+k_fused_batch(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
+              const BatchRun<real> *__restrict__ runs, const int *__restrict__ tile_start, int nruns, int total,
+              real ca, real cb, real ccoef)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto &sm = *reinterpret_cast<FusedSmem<real, TX, TY, KP> *>(smem_raw);
+    __shared__ __align__(16) BatchRun<real> run;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        int lo = 0, hi = nruns - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(tile_start + mid) <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        {
+            const int4 *src = reinterpret_cast<const int4 *>(runs + lo);
+            int4 *dst = reinterpret_cast<int4 *>(&run);
+            for (int w = threadIdx.x; w < (int)(sizeof(BatchRun<real>) / sizeof(int4)); w += blockDim.x)
+                dst[w] = __ldg(src + w);
+        }
+        __syncthreads();
+        const int lt = item - __ldg(tile_start + lo);
+        const int x0 = (lt % run.ntx) * TX, y0 = (lt / run.ntx) * TY;
+        stage_tile<real, TX, TY, KP>(sm, fs + run.off, fn + run.off, out + run.off, status + lo, run.g, run.t, x0, y0,
+                                     ca, cb, ccoef * (real)run.g.dt);
+        __syncthreads();  // the next item overwrites the shared staging
+    }
+}
+
 template <typename real, int TX, int TY, int KP>
 cudaError_t fused_prepare_one()
 {
-    return cudaFuncSetAttribute(k_fused<real, TX, TY, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_fused<real, TX, TY, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(FusedSmem<real, TX, TY, KP>));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fused_batch<real, TX, TY, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(FusedSmem<real, TX, TY, KP>));
+}
+
+template <typename real, int TX, int TY, int KP>
+cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, int *status, const void *runs,
+                                   const int *tile_start, int nruns, int total, StageCoef c, cudaStream_t s)
+{
+    static int ctas_per_sm[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &per = ctas_per_sm[dev & 63];
+    if (per == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per, k_fused_batch<real, TX, TY, KP>, TX * TY * KP, sizeof(FusedSmem<real, TX, TY, KP>));
+        if (e != cudaSuccess || per < 1) per = 1;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = total < per * sms ? total : per * sms;
+    if (grid < 1) return cudaSuccess;
+    k_fused_batch<real, TX, TY, KP><<<grid, TX * TY * KP, sizeof(FusedSmem<real, TX, TY, KP>), s>>>(
+        fs, fn, out, status, static_cast<const BatchRun<real> *>(runs), tile_start, nruns, total, (real)c.ca,
+        (real)c.cb, (real)c.cc);
+    return cudaGetLastError();
 }
 
 template <typename real, int TX, int TY, int KP>
@@ -355,6 +437,9 @@ cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *sta
     if (tx == A && ty == B && kp == C) return fused_prepare_one<real, A, B, C>();
 #define OLB_FUSED_LAUNCH_CASE(real, A, B, C) \
     if (tx == A && ty == B && kp == C) return fused_launch_one<real, A, B, C>(fs, fn, out, status, g, t, c, s);
+#define OLB_FUSED_BATCH_CASE(real, A, B, C)                                                                  \
+    if (tx == A && ty == B && kp == C)                                                                       \
+        return fused_batch_launch_one<real, A, B, C>(fs, fn, out, status, runs, tile_start, nruns, total, c, s);
 #define OLB_DEFINE_FUSED(real)                                                                                \
     cudaError_t prepare_fused(real *, int tx, int ty, int kp)                                                 \
     {                                                                                                         \
@@ -366,6 +451,23 @@ cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *sta
     {                                                                                                         \
         OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_LAUNCH_CASE)                                                    \
         return cudaErrorInvalidValue;                                                                         \
+    }                                                                                                         \
+    cudaError_t launch_fused_batch(const real *fs, const real *fn, real *out, int *status, const void *runs,  \
+                                   const int *tile_start, int nruns, int total, StageCoef c, int tx, int ty,  \
+                                   int kp, cudaStream_t s)                                                    \
+    {                                                                                                         \
+        OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_BATCH_CASE)                                                     \
+        return cudaErrorInvalidValue;                                                                         \
+    }                                                                                                         \
+    size_t batch_run_bytes(real *) { return sizeof(BatchRun<real>); }                                         \
+    void batch_run_fill(real *, void *dst, const Geo &g, const Tab<real> &t, long long off, int ntx)         \
+    {                                                                                                         \
+        BatchRun<real> r{};                                                                                   \
+        r.g = g;                                                                                              \
+        r.t = t;                                                                                              \
+        r.off = off;                                                                                          \
+        r.ntx = ntx;                                                                                          \
+        *static_cast<BatchRun<real> *>(dst) = r;                                                              \
     }
 
 }  // namespace olb

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct olb_params;
+
 namespace olb {
 
 constexpr int NQ = 5;   // Gauss-Hermite points per axis (Table trots)
@@ -46,6 +48,11 @@ double host_g(const HostTables &t, int k, double u, double T);
 template <typename real>
 void fill_tab(Tab<real> *tab, const HostTables &h, const double Tw[2], const double uw[2]);
 
+// Parameter validation of olb_create (OLB_OK / OLB_ERR_ARG / OLB_ERR_CFL)
+// and the mapping of CUDA errors to status codes (olb_api.cu).
+int validate_params(const ::olb_params *p);
+int cuda_status(cudaError_t e);
+
 // RK-3 stage coefficients: out = ca f^n + cb f_s + cc L[f_s] (Eq. rk3).
 struct StageCoef {
     double ca, cb, cc;
@@ -57,6 +64,11 @@ struct StageCoef {
     cudaError_t prepare_fused(real *, int tx, int ty, int kp);                                         \
     cudaError_t launch_fused(const real *fs, const real *fn, real *out, int *status, const Geo &g,     \
                              const Tab<real> &t, StageCoef c, int tx, int ty, int kp, cudaStream_t s); \
+    cudaError_t launch_fused_batch(const real *fs, const real *fn, real *out, int *status,             \
+                                   const void *runs, const int *tile_start, int nruns, int total,      \
+                                   StageCoef c, int tx, int ty, int kp, cudaStream_t s);               \
+    size_t batch_run_bytes(real *);                                                                    \
+    void batch_run_fill(real *, void *dst, const Geo &g, const Tab<real> &t, long long off, int ntx);  \
     cudaError_t launch_init(real *f, const double *n, const double *ux, const double *uy,              \
                             const double *T, const Geo &g, const Tab<real> &t, cudaStream_t s);         \
     cudaError_t launch_moments_out(const real *f, double *n, double *ux, double *uy, double *T,        \

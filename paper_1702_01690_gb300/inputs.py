@@ -207,3 +207,46 @@ def phase_separation(n: int = 4096, Tw: float = 0.7, steps: int = 10000) -> tupl
                   Tw=(Tw, Tw), side_x=1, steps=steps,
                   name=f"phase separation {n}^2 Tw={Tw}")
     return p, cold_rest(n, n, ds, SEED_BASE + 5, 1.0, 0.01, 1.0)
+
+
+def stable_dt(ds: float, sigma: float = 1e-4, n_max: float = 1.0, cfl: float = 0.146,
+              omega_dt: float = 0.7) -> float:
+    """Largest dt with p_max dt / ds <= cfl and 2-D capillary omega dt <= omega_dt
+    (omega ~ 2 x 2.7 sqrt(sigma n_max) / ds^2, see the module docstring)."""
+    dt = cfl * ds / P_MAX
+    if sigma > 0:
+        dt = min(dt, omega_dt / (5.4 * math.sqrt(sigma * n_max) / ds ** 2))
+    return dt
+
+
+def batch_sweep(max_n: int = 1024) -> list:
+    """The 64 independent runs of the batched workload (sizes capped at max_n):
+    22 shear waves (N in 32 .. 1024, T0 = 0.8 and 1.1), 11 longitudinal waves
+    (T0 = 1.1), 15 Laplace drops (R = 0.1 .. 0.3 on 256^2 .. 1024^2, T = 0.9)
+    and 16 planar wall runs (T_w = 0.75 .. 0.9 on nx = 256 .. 2048, ny = 8);
+    amplitude 1e-3, tau = 0.01 for the waves, dt = stable_dt per run."""
+    runs = []
+    sizes = [n for n in (32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024) if n <= max_n]
+    for T0 in (0.8, 1.1):
+        for N in sizes:
+            ds = 1.0 / N
+            p = RunParams(nx=N, ny=N, ds=ds, dt=stable_dt(ds), tau=0.01, name=f"shear {N}^2 T0={T0}")
+            runs.append((p, shear_wave(N, N, ds, 1.0, T0, 1e-3)))
+    for N in sizes:
+        ds = 1.0 / N
+        p = RunParams(nx=N, ny=N, ds=ds, dt=stable_dt(ds), tau=0.01, name=f"longitudinal {N}^2")
+        runs.append((p, longitudinal_wave(N, N, ds, 1.0, 1.1, 1e-3)))
+    for R in (0.1, 0.15, 0.2, 0.25, 0.3):
+        for N in (256, 512, 1024):
+            N = min(N, max_n)
+            ds = 1.0 / N
+            p = RunParams(nx=N, ny=N, ds=ds, dt=stable_dt(ds, n_max=1.66), tau=5e-3, name=f"Laplace {N}^2 R={R}")
+            runs.append((p, laplace_drop(N, N, ds, R, 0.9)))
+    for Tw in (0.75, 0.8, 0.85, 0.9):
+        for nx in (256, 512, 1024, 2048):
+            nx = min(nx, 2 * max_n)
+            ds = 1.0 / nx
+            p = RunParams(nx=nx, ny=8, ds=ds, dt=stable_dt(ds, n_max=2.2), tau=0.005, Tw=(Tw, Tw), side_x=1,
+                          name=f"planar {nx}x8 Tw={Tw}")
+            runs.append((p, cold_rest(nx, 8, ds, SEED_BASE + 4, 1.0, 0.01, 1.0)))
+    return runs

@@ -29,7 +29,11 @@ WENO_JS = 0
 SYMBOLS = ("olb_set_allocator", "olb_create", "olb_destroy", "olb_init_fields",
            "olb_init_fields_device", "olb_step", "olb_step_async", "olb_get_status",
            "olb_moments", "olb_moments_device", "olb_get_populations",
-           "olb_set_populations", "olb_status_string", "olb_profile", "olb_set_tile", "olb_get_tile", "olb_step_static")
+           "olb_set_populations", "olb_status_string", "olb_profile", "olb_set_tile", "olb_get_tile", "olb_step_static",
+           "olb_batch_create", "olb_batch_destroy", "olb_batch_init_fields", "olb_batch_step",
+           "olb_batch_step_async", "olb_batch_get_status", "olb_batch_moments",
+           "olb_batch_get_populations", "olb_batch_set_tile", "olb_batch_get_tile",
+           "olb_batch_autotune", "olb_batch_profile")
 
 
 class Params(ctypes.Structure):
@@ -73,6 +77,30 @@ _lib.olb_profile.restype = ctypes.c_int
 _lib.olb_step_static.argtypes = [ctypes.POINTER(Params), _VP, _VP, ctypes.c_int]
 _lib.olb_step_static.restype = ctypes.c_int
 STATIC_MAX_NODES = 16384
+_lib.olb_batch_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int, _VP, ctypes.POINTER(_VP)]
+_lib.olb_batch_create.restype = ctypes.c_int
+_lib.olb_batch_destroy.argtypes = [_VP]
+_lib.olb_batch_destroy.restype = None
+_lib.olb_batch_init_fields.argtypes = [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]
+_lib.olb_batch_init_fields.restype = ctypes.c_int
+_lib.olb_batch_moments.argtypes = [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]
+_lib.olb_batch_moments.restype = ctypes.c_int
+for _n in ("olb_batch_step", "olb_batch_step_async"):
+    getattr(_lib, _n).argtypes = [_VP, ctypes.c_int]
+    getattr(_lib, _n).restype = ctypes.c_int
+_lib.olb_batch_get_status.argtypes = [_VP, _VP]
+_lib.olb_batch_get_status.restype = ctypes.c_int
+_lib.olb_batch_get_populations.argtypes = [_VP, ctypes.c_int, _VP]
+_lib.olb_batch_get_populations.restype = ctypes.c_int
+_lib.olb_batch_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+_lib.olb_batch_set_tile.restype = ctypes.c_int
+for _n in ("olb_batch_get_tile",):
+    getattr(_lib, _n).argtypes = [_VP, _VP, _VP, _VP]
+    getattr(_lib, _n).restype = ctypes.c_int
+_lib.olb_batch_autotune.argtypes = [_VP, ctypes.c_int, _VP, _VP, _VP]
+_lib.olb_batch_autotune.restype = ctypes.c_int
+_lib.olb_batch_profile.argtypes = [_VP, ctypes.c_int, _VP]
+_lib.olb_batch_profile.restype = ctypes.c_int
 _lib.olb_status_string.argtypes = [ctypes.c_int]
 _lib.olb_status_string.restype = ctypes.c_char_p
 
@@ -247,3 +275,79 @@ class Context:
 
 def create(run, precision: int = FP64, stream=None) -> Context:
     return Context(params_from(run, precision), stream)
+
+
+class Batch:
+    """One olb_batch: independent runs of uneven sizes advanced together."""
+
+    def __init__(self, runs, precision: int = FP64, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        plist = [params_from(r, precision) for r in runs]
+        arr = (Params * len(plist))(*plist)
+        self.shapes = [(p.ny, p.nx) for p in plist]
+        h = _VP()
+        _check(_lib.olb_batch_create(arr, len(plist), _VP(stream.cuda_stream), ctypes.byref(h)),
+               "olb_batch_create")
+        self._h = h
+
+    @property
+    def count(self) -> int:
+        return len(self.shapes)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.olb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, run: int, n, ux, uy, T):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self.shapes[run]) for a in (n, ux, uy, T)]
+        _check(_lib.olb_batch_init_fields(self._h, int(run), *[_host_ptr(a) for a in arrs]),
+               "olb_batch_init_fields")
+
+    def step(self, nsteps: int = 1) -> int:
+        return _check(_lib.olb_batch_step(self._h, int(nsteps)), "olb_batch_step")
+
+    def step_async(self, nsteps: int = 1) -> None:
+        _check(_lib.olb_batch_step_async(self._h, int(nsteps)), "olb_batch_step_async")
+
+    def status(self):
+        per = np.zeros(self.count, dtype=np.int32)
+        rc = _lib.olb_batch_get_status(self._h, per.ctypes.data_as(_VP))
+        return rc, per
+
+    def moments(self, run: int):
+        out = [np.zeros(self.shapes[run]) for _ in range(4)]
+        _check(_lib.olb_batch_moments(self._h, int(run), *[_host_ptr(a) for a in out]), "olb_batch_moments")
+        return tuple(out)
+
+    def get_populations(self, run: int) -> np.ndarray:
+        out = np.zeros((25,) + self.shapes[run])
+        _check(_lib.olb_batch_get_populations(self._h, int(run), _host_ptr(out)), "olb_batch_get_populations")
+        return out
+
+    def set_tile(self, tx: int, ty: int, kp: int) -> None:
+        _check(_lib.olb_batch_set_tile(self._h, int(tx), int(ty), int(kp)), "olb_batch_set_tile")
+
+    def get_tile(self):
+        v = [ctypes.c_int() for _ in range(3)]
+        _check(_lib.olb_batch_get_tile(self._h, *[ctypes.byref(x) for x in v]), "olb_batch_get_tile")
+        return tuple(x.value for x in v)
+
+    def autotune(self, nsteps: int = 3):
+        v = [ctypes.c_int() for _ in range(3)]
+        _check(_lib.olb_batch_autotune(self._h, int(nsteps), *[ctypes.byref(x) for x in v]), "olb_batch_autotune")
+        return tuple(x.value for x in v)
+
+    def profile(self, nsteps: int) -> float:
+        ms = ctypes.c_double()
+        _check(_lib.olb_batch_profile(self._h, int(nsteps), ctypes.byref(ms)), "olb_batch_profile")
+        return ms.value
