@@ -347,13 +347,18 @@ k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict_
 // the first item of run r (prefix sum, tile_start[nruns] = total).  Each run
 // has its populations at offset `off` of the three shared buffers and its own
 // status word.
+// 16-byte aligned and sized: the kernel copies one descriptor into shared
+// memory with 16-byte loads, so consecutive array elements must stay aligned
+// and the whole struct must be covered by whole int4 words.
 template <typename real>
-struct BatchRun {
+struct __align__(16) BatchRun {
     Geo g;
     Tab<real> t;
     long long off;
     int ntx, pad;
 };
+static_assert(sizeof(BatchRun<double>) % 16 == 0, "BatchRun<double> must be a whole number of int4 words");
+static_assert(sizeof(BatchRun<float>) % 16 == 0, "BatchRun<float> must be a whole number of int4 words");
 
 template <typename real, int TX, int TY, int KP>
 __global__ void __launch_bounds__(TX *TY *KP)

@@ -226,7 +226,7 @@ def batch_sweep(max_n: int = 1024) -> list:
     and 16 planar wall runs (T_w = 0.75 .. 0.9 on nx = 256 .. 2048, ny = 8);
     amplitude 1e-3, tau = 0.01 for the waves, dt = stable_dt per run."""
     runs = []
-    sizes = [n for n in (32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024) if n <= max_n]
+    sizes = [min(n, max_n) for n in (32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024)]
     for T0 in (0.8, 1.1):
         for N in sizes:
             ds = 1.0 / N
