@@ -25,16 +25,44 @@
 
 namespace olb {
 
+// n and Delta p of the region, kept for the 49-point stencils.  The stencils
+// cancel to O(ds^k) of their terms on fine grids, so the FP32 kernel keeps
+// each value as an unevaluated sum hi + lo of two floats (hi = the value
+// rounded to FP32, lo = the FP64 remainder rounded to FP32): differences of
+// neighbouring values then keep ~FP64 accuracy at FP32 cost.
+template <typename real>
+struct FieldT {
+    using type = double;
+};
+template <>
+struct FieldT<float> {
+    using type = float2;
+};
+
+__device__ __forceinline__ double make_field(double v, double) { return v; }
+__device__ __forceinline__ float2 make_field(double v, float)
+{
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+__device__ __forceinline__ double field_diff(double a, double b) { return a - b; }
+__device__ __forceinline__ float field_diff(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
+__device__ __forceinline__ double field_val(double a) { return a; }
+__device__ __forceinline__ float field_val(float2 a) { return a.x + a.y; }
+
 template <typename real, int TX, int TY, int KP>
 struct FusedSmem {
     static constexpr int HX = TX + 8, HY = TY + 6, NN = TX * TY, NT = NN * KP;
+    using fld = typename FieldT<real>::type;
     real pop[NK][HY][HX];
-    real n[HY][HX];
-    real dp[HY][HX];
+    fld n[HY][HX];
+    fld dp[HY][HX];
     real ux[TY][TX];
     real uy[TY][TX];
     real T[TY][TX];
-    real loc[3 + 2 * NQ][NN];  // F_x, F_y, n, g_k(u_x, T), g_k(u_y, T) per tile node
+    // F_x, F_y, n, g_k(u_x, T), g_k(u_y, T) per tile node, shared by the KP
+    // velocity lanes (with one lane they stay in registers)
+    real loc[KP > 1 ? 3 + 2 * NQ : 1][KP > 1 ? NN : 1];
     real fx[KP][TY][TX + 1];
     real fy[KP][TY + 1][TX];
     real nw[2][TY];
@@ -139,8 +167,8 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
         const double T = 0.5 * (en * inv_n - ux * ux - uy * uy);
         // Delta p = n T - p^w, p^w = n T / (1 - b n) - a n^2 (Eq. vdw)
         const double nT = n * T;
-        sm.n[r][c] = (real)n;
-        sm.dp[r][c] = (real)(nT - fma(nT, recip_nr(1.0 - g.b * n), -g.a * n * n));
+        sm.n[r][c] = make_field(n, real(0));
+        sm.dp[r][c] = make_field(nT - fma(nT, recip_nr(1.0 - g.b * n), -g.a * n * n), real(0));
         const int tr = r - 3, tc = c - 4;
         if (tr >= 0 && tr < TY && tc >= 0 && tc < TX) {
             sm.ux[tr][tc] = (real)ux;
@@ -236,6 +264,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     __syncthreads();
 
     // ---- 4. force and equilibrium factors at the tile nodes (lane 0)
+    real Fx = 0, Fy = 0, nn = 1, gx[NQ], gy[NQ];
     if (active && lane_k == 0) {
         real ddx = 0, ddy = 0, ldx = 0, ldy = 0;
         constexpr int cy = 3, cx = 4;
@@ -246,27 +275,31 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 const int am = m < 0 ? -m : m;
                 if (grad_w(l, am) != 0.0) {
                     const real w = real(l * grad_w(l, am));
-                    ddx += w * (sm.dp[ty + cy + m][tx + cx + l] - sm.dp[ty + cy + m][tx + cx - l]);
-                    ddy += w * (sm.dp[ty + cy + l][tx + cx + m] - sm.dp[ty + cy - l][tx + cx + m]);
+                    ddx += w * field_diff(sm.dp[ty + cy + m][tx + cx + l], sm.dp[ty + cy + m][tx + cx - l]);
+                    ddy += w * field_diff(sm.dp[ty + cy + l][tx + cx + m], sm.dp[ty + cy - l][tx + cx + m]);
                 }
                 if (glap_c(am, l) != 0.0) {
                     const real w = real(glap_c(am, l));
-                    ldx += w * (sm.n[ty + cy + m][tx + cx + l] - sm.n[ty + cy + m][tx + cx - l]);
-                    ldy += w * (sm.n[ty + cy + l][tx + cx + m] - sm.n[ty + cy - l][tx + cx + m]);
+                    ldx += w * field_diff(sm.n[ty + cy + m][tx + cx + l], sm.n[ty + cy + m][tx + cx - l]);
+                    ldy += w * field_diff(sm.n[ty + cy + l][tx + cx + m], sm.n[ty + cy - l][tx + cx + m]);
                 }
             }
-        const real nn = sm.n[ty + cy][tx + cx];
+        nn = field_val(sm.n[ty + cy][tx + cx]);
         const real dn = real(g.inv_ds) / nn;
-        sm.loc[0][node] = ddx * dn + real(g.sigma) * ldx * real(g.inv_ds3);
-        sm.loc[1][node] = ddy * dn + real(g.sigma) * ldy * real(g.inv_ds3);
-        sm.loc[2][node] = nn;
-        real gq[NQ];
-        eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], gq);
+        Fx = ddx * dn + real(g.sigma) * ldx * real(g.inv_ds3);
+        Fy = ddy * dn + real(g.sigma) * ldy * real(g.inv_ds3);
+        eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], gx);
+        eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gy);
+        if constexpr (KP > 1) {
+            sm.loc[0][node] = Fx;
+            sm.loc[1][node] = Fy;
+            sm.loc[2][node] = nn;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) sm.loc[3 + q][node] = gq[q];
-        eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gq);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) sm.loc[3 + NQ + q][node] = gq[q];
+            for (int q = 0; q < NQ; ++q) {
+                sm.loc[3 + q][node] = gx[q];
+                sm.loc[3 + NQ + q][node] = gy[q];
+            }
+        }
     }
 
     // ---- 5. advection, collision and RK combination, KP velocities at a time
@@ -319,11 +352,20 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 dy += t.D[k2][q] * sm.pop[NQ * k1 + q][r][c];
             }
             const real f = sm.pop[k][r][c];
-            const real feq = sm.loc[2][node] * sm.loc[3 + k1][node] * sm.loc[3 + NQ + k2][node];
+            real feq, fxv, fyv;
+            if constexpr (KP > 1) {
+                feq = sm.loc[2][node] * sm.loc[3 + k1][node] * sm.loc[3 + NQ + k2][node];
+                fxv = sm.loc[0][node];
+                fyv = sm.loc[1][node];
+            } else {
+                feq = nn * sel5(gx, k1) * sel5(gy, k2);
+                fxv = Fx;
+                fyv = Fy;
+            }
             real adv = 0;
             if (k1 != 2) adv += t.R[k1] * (sm.fx[lane_k][ty][tx + 1] - sm.fx[lane_k][ty][tx]);
             if (k2 != 2) adv += t.R[k2] * (sm.fy[lane_k][ty + 1][tx] - sm.fy[lane_k][ty][tx]);
-            const real Lloc = -(sm.loc[0][node] * dx + sm.loc[1][node] * dy) - (f - feq) * itau;
+            const real Lloc = -(fxv * dx + fyv * dy) - (f - feq) * itau;
             real v = cb * f + cc * Lloc - cadv * adv;
             if (ca != real(0)) v += ca * fn[k * g.plane + o];
             out[k * g.plane + o] = v;

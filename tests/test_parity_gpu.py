@@ -333,3 +333,20 @@ def test_every_tile_shape_gives_identical_results(olb, side_x):
         ctx.set_tile(32, 16, 1)
     c32 = olb.create(p, olb.FP32_KAHAN)
     c32.set_tile(32, 16, 1)
+
+
+def test_fp32_kahan_fine_grid_laplace(olb):
+    """FP32 + Kahan against the FP64 path on the Laplace drop at 1024^2 (fine
+    grid, where the capillary stencil cancels to O(ds^3) of its terms): n, T
+    within 1e-5; u, created by the force in these few steps, within 1e-3."""
+    p, fl = inputs.laplace(1024, R=0.2, steps=10)
+    a = olb.create(p)
+    a.init_fields(*fl)
+    a.step(10)
+    b = olb.create(p, olb.FP32_KAHAN)
+    b.init_fields(*fl)
+    b.step(10)
+    err = moments_rel(b.moments(), a.moments())
+    print("fp32 vs fp64 after 10 steps:", err)
+    assert err["n"] < 1e-5 and err["T"] < 1e-5, err
+    assert err["u"] < 1e-3, err
