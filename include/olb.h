@@ -71,7 +71,10 @@ enum {
 
 /* Non-linear WENO weights. */
 enum {
-    OLB_WENO_JS = 0     /* Jiang-Shu weights of Eq. weno5_omega, Table tab:weno */
+    OLB_WENO_JS = 0,     /* Jiang-Shu weights of Eq. weno5_omega, Table tab:weno */
+    OLB_WENO_LEARNED = 1 /* weights from a trained network (olb_set_weno_mlp), with the
+                            Jiang-Shu weights and Table tab:weno wherever a smoothness
+                            indicator vanishes; single contexts only */
 };
 
 /* Problem statement (Sec. 2, Sec. 3).  Walls: index 0 is the wall at x = 0,
@@ -89,7 +92,7 @@ typedef struct olb_params {
     int side_x;         /* OLB_SIDE_PERIODIC or OLB_SIDE_DIFFUSE */
     int side_y;         /* OLB_SIDE_PERIODIC */
     int precision;      /* OLB_FP64 or OLB_FP32_KAHAN */
-    int weno_mode;      /* OLB_WENO_JS */
+    int weno_mode;      /* OLB_WENO_JS or OLB_WENO_LEARNED */
 } olb_params;
 
 typedef struct olb_ctx olb_ctx;
@@ -226,6 +229,41 @@ int olb_batch_autotune(olb_batch *b, int nsteps, int *tx, int *ty, int *kp);
 /* Mean device time (ms) of one stage launch over nsteps individually
  * launched steps (the runs advance). */
 int olb_batch_profile(olb_batch *b, int nsteps, double *ms);
+
+/* ------------------------------------------------------------------------
+ * Learned WENO-5 weights.  Not part of the paper: a 5-32-32-3 network (tanh,
+ * tanh, softmax) maps the normalised stencil x = (v - mean v)/(max v - min v)
+ * of an interface to three convex weights that replace the Jiang-Shu weights
+ * of Eq. weno5_omega.  Parameters: OLB_MLP_PARAMS floats, W1 [32][5], b1 [32],
+ * W2 [32][32], b2 [32], W3 [3][32], b3 [3] (row-major, concatenated).
+ * Training objective: the mean over samples of (sum_q w_q gn_q - tn)^2, where
+ * gn_q are the three candidate values of Eq. weno5_flux minus the centre
+ * value and tn the target interface value minus the centre value, both
+ * divided by max v - min v.  All arrays of these calls are device pointers
+ * (FP32, sample-major: x [n][5], gn [n][3], tn [n], w [n][3]); each call
+ * runs on `stream` and returns after its work is complete.
+ * ------------------------------------------------------------------------ */
+#define OLB_MLP_PARAMS 1347
+
+/* Weights w of n normalised stencils x. */
+int olb_mlp_forward(const float *theta, const float *x, int n, float *w, void *stream);
+
+/* Mean loss over the n samples into *loss (device float) and its gradient
+ * with respect to theta into grad (device, OLB_MLP_PARAMS floats). */
+int olb_mlp_grad(const float *theta, const float *x, const float *gn, const float *tn, int n,
+                 float *grad, float *loss, void *stream);
+
+/* Train theta in place with Adam (beta 0.9 / 0.999, eps 1e-8, learning rate
+ * lr) over `epochs` passes of consecutive minibatches of `batch` samples;
+ * loss_history (host, `epochs` floats, or NULL) receives each epoch's mean
+ * minibatch loss.  Allocates its optimiser state with cudaMalloc. */
+int olb_mlp_train(float *theta, const float *x, const float *gn, const float *tn, int n, int epochs,
+                  int batch, float lr, void *stream, float *loss_history);
+
+/* Load the network (host, OLB_MLP_PARAMS floats) into a context created with
+ * weno_mode OLB_WENO_LEARNED; olb_step returns OLB_ERR_STATE until this is
+ * done.  OLB_ERR_STATE for other contexts, OLB_ERR_ARG for non-finite values. */
+int olb_set_weno_mlp(olb_ctx *ctx, const float *theta);
 
 /* Largest grid (nx * ny nodes) olb_step_static accepts. */
 #define OLB_STATIC_MAX_NODES 16384

@@ -22,6 +22,9 @@ Parity status of each oracle function (what pins it, see tests/test_oracle_*):
   orc_glap_stencil             -- same, for grad(Laplacian)
   orc_weno5                    -- Table tab:weno, exactness on quadratics,
                                   5th-order linear limit, convergence on sines
+  orc_weno5_learned, mlp.py    -- mlp.grad against central finite differences;
+                                  the C forward against mlp.py; Table tab:weno
+                                  wherever an indicator vanishes
   orc_step                     -- conservation of mass; rest state is a fixed
                                   point; shear-wave decay rate (Eq. shear_sol);
                                   self-convergence order in ds; n_w zero net flux
@@ -105,6 +108,9 @@ def lib():
             L.orc_set_f.argtypes = [ctypes.c_void_p, _D]
             L.orc_get_moments.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
             L.orc_eval.argtypes = [ctypes.c_void_p, _D, _D, _D]
+            L.orc_weno5_learned.restype = ctypes.c_double
+            L.orc_weno5_learned.argtypes = [_D, _D, _D]
+            L.orc_set_mlp.argtypes = [ctypes.c_void_p, _D]
             L.orc_set_threads.argtypes = [ctypes.c_int]
             L.orc_max_threads.restype = ctypes.c_int
             _lib = L
@@ -180,6 +186,14 @@ def weno5(v, return_weights: bool = False):
     return (val, w) if return_weights else val
 
 
+def weno5_learned(theta, v, return_weights: bool = False):
+    theta = _f64(theta)
+    v = _f64(v)
+    w = np.zeros(3)
+    val = lib().orc_weno5_learned(_p(theta), _p(v), _p(w))
+    return (val, w) if return_weights else val
+
+
 def set_threads(n: int) -> None:
     lib().orc_set_threads(int(n))
 
@@ -232,6 +246,14 @@ class Oracle:
 
     def step(self, nsteps: int = 1):
         lib().orc_step(self._h, int(nsteps))
+
+    def set_mlp(self, theta=None):
+        """Learned WENO weights with parameters theta (None: Jiang-Shu)."""
+        if theta is None:
+            lib().orc_set_mlp(self._h, None)
+        else:
+            self._mlp = _f64(theta)
+            lib().orc_set_mlp(self._h, _p(self._mlp))
 
     def moments(self):
         out = [np.zeros(self._shape()) for _ in range(4)]

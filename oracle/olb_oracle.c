@@ -296,6 +296,65 @@ double orc_weno5(const double *v, double *wout)
     return w1 * F1 + w2 * F2 + w3 * F3;
 }
 
+/* Learned weights (the network described in oracle/mlp.py): the same
+ * interface value with the three weights produced by a 5-32-32-3 MLP
+ * (tanh, tanh, softmax) from the normalised stencil (v - mean)/(max - min).
+ * Where any indicator vanishes, Table tab:weno applies as in orc_weno5, so
+ * constant ghost layers keep their exact fluxes.  theta: 1347 parameters,
+ * W1 [32][5], b1 [32], W2 [32][32], b2 [32], W3 [3][32], b3 [3]. */
+#define MLP_H 32
+double orc_weno5_learned(const double *theta, const double *v, double *wout)
+{
+    double sg[3];
+    sg[0] = 13.0 / 12.0 * (v[0] - 2.0 * v[1] + v[2]) * (v[0] - 2.0 * v[1] + v[2])
+          + 0.25 * (v[0] - 4.0 * v[1] + 3.0 * v[2]) * (v[0] - 4.0 * v[1] + 3.0 * v[2]);
+    sg[1] = 13.0 / 12.0 * (v[1] - 2.0 * v[2] + v[3]) * (v[1] - 2.0 * v[2] + v[3])
+          + 0.25 * (v[1] - v[3]) * (v[1] - v[3]);
+    sg[2] = 13.0 / 12.0 * (v[2] - 2.0 * v[3] + v[4]) * (v[2] - 2.0 * v[3] + v[4])
+          + 0.25 * (3.0 * v[2] - 4.0 * v[3] + v[4]) * (3.0 * v[2] - 4.0 * v[3] + v[4]);
+    if (sg[0] == 0.0 || sg[1] == 0.0 || sg[2] == 0.0) return orc_weno5(v, wout);
+    const double *W1 = theta, *b1 = theta + 160, *W2 = theta + 192, *b2 = theta + 1216;
+    const double *W3 = theta + 1248, *b3 = theta + 1344;
+    double mean = 0.0, mx = v[0], mn = v[0];
+    for (int q = 0; q < 5; ++q) {
+        mean += v[q];
+        if (v[q] > mx) mx = v[q];
+        if (v[q] < mn) mn = v[q];
+    }
+    mean /= 5.0;
+    double x[5];
+    for (int q = 0; q < 5; ++q) x[q] = (v[q] - mean) / (mx - mn);
+    double h1[MLP_H], h2[MLP_H], z[3];
+    for (int j = 0; j < MLP_H; ++j) {
+        double a = b1[j];
+        for (int q = 0; q < 5; ++q) a += W1[j * 5 + q] * x[q];
+        h1[j] = tanh(a);
+    }
+    for (int j = 0; j < MLP_H; ++j) {
+        double a = b2[j];
+        for (int k = 0; k < MLP_H; ++k) a += W2[j * MLP_H + k] * h1[k];
+        h2[j] = tanh(a);
+    }
+    double zmax = -1e300;
+    for (int q = 0; q < 3; ++q) {
+        double a = b3[q];
+        for (int j = 0; j < MLP_H; ++j) a += W3[q * MLP_H + j] * h2[j];
+        z[q] = a;
+        if (a > zmax) zmax = a;
+    }
+    double w[3], sum = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        w[q] = exp(z[q] - zmax);
+        sum += w[q];
+    }
+    for (int q = 0; q < 3; ++q) w[q] /= sum;
+    double F1 = v[0] / 3.0 - 7.0 / 6.0 * v[1] + 11.0 / 6.0 * v[2];
+    double F2 = -v[1] / 6.0 + 5.0 / 6.0 * v[2] + v[3] / 3.0;
+    double F3 = v[2] / 3.0 + 5.0 / 6.0 * v[3] - v[4] / 6.0;
+    if (wout) { wout[0] = w[0]; wout[1] = w[1]; wout[2] = w[2]; }
+    return w[0] * F1 + w[1] * F2 + w[2] * F3;
+}
+
 /* ------------------------------------------------------------------ */
 /* Solver context                                                      */
 /* ------------------------------------------------------------------ */
@@ -319,6 +378,8 @@ typedef struct orc_ctx {
     double geqw[2][K];                 /* g_{k1}(0,Tw) g_{k2}(uw,Tw) per wall */
     double denw[2];                    /* denominator of Eq. nw per wall */
     double cgrad[49], cglap[49];
+    int learned;                       /* 1: learned weights (orc_set_mlp) */
+    double mlp[1347];
 } orc_ctx;
 
 static int wrap(int i, int n)
@@ -426,7 +487,7 @@ static double flux_x(const orc_ctx *c, const double *fs, int kap, int i, int j)
     } else {
         return 0.0;
     }
-    return px * orc_weno5(v, NULL);
+    return px * (c->learned ? orc_weno5_learned(c->mlp, v, NULL) : orc_weno5(v, NULL));
 }
 
 /* y-flux at the face y = j ds between rows j-1 and j (y always periodic). */
@@ -442,7 +503,7 @@ static double flux_y(const orc_ctx *c, const double *fs, int kap, int i, int j)
     } else {
         return 0.0;
     }
-    return py * orc_weno5(v, NULL);
+    return py * (c->learned ? orc_weno5_learned(c->mlp, v, NULL) : orc_weno5(v, NULL));
 }
 
 /* Field value with the boundary rule of Sec. 3.4.3: even reflection about
@@ -570,6 +631,15 @@ static void rk3_step(orc_ctx *c)
 /* ------------------------------------------------------------------ */
 /* Exported driver calls                                               */
 /* ------------------------------------------------------------------ */
+
+/* Switch the context to learned WENO weights with parameters theta
+ * (1347 values), or back to Jiang-Shu weights when theta is NULL. */
+void orc_set_mlp(orc_ctx *c, const double *theta)
+{
+    if (!theta) { c->learned = 0; return; }
+    memcpy(c->mlp, theta, sizeof c->mlp);
+    c->learned = 1;
+}
 
 void orc_set_threads(int nthreads)
 {

@@ -122,6 +122,8 @@ struct olb_ctx {
     void *f[3];                 // f^n, f^(1), f^(2)
     int *status;
     int tx, ty, kp;             // stage-kernel tile shape and velocity lanes
+    float *mlp;                 // learned WENO weights: network parameters
+    bool mlp_set;
     double *stage4;             // FP64 [4][ny][nx] staging for host transfers
     struct Alloc {
         void *ptr;
@@ -188,7 +190,8 @@ static cudaError_t enqueue_stage(olb_ctx *c, int st, cudaStream_t s)
     real *dst[3] = {f1, f2, f0};
     StageCoef coef;
     stage_coef(c->p.dt, st, &coef);
-    return launch_fused(src[st], f0, dst[st], c->status, c->geo, ctx_tab<real>(c), coef, c->tx, c->ty, c->kp, s);
+    return launch_fused(src[st], f0, dst[st], c->status, c->geo, ctx_tab<real>(c), coef, c->tx, c->ty, c->kp,
+                        c->p.weno_mode == OLB_WENO_LEARNED ? c->mlp : nullptr, s);
 }
 
 template <typename real>
@@ -257,7 +260,7 @@ int olb::validate_params(const olb_params *p)
     if (p->side_y != OLB_SIDE_PERIODIC) return OLB_ERR_ARG;
     if (p->side_x == OLB_SIDE_DIFFUSE && p->nx < 3) return OLB_ERR_ARG;
     if (p->precision != OLB_FP64 && p->precision != OLB_FP32_KAHAN) return OLB_ERR_ARG;
-    if (p->weno_mode != OLB_WENO_JS) return OLB_ERR_ARG;
+    if (p->weno_mode != OLB_WENO_JS && p->weno_mode != OLB_WENO_LEARNED) return OLB_ERR_ARG;
     if (!(p->ds > 0.0) || !(p->dt > 0.0) || !(p->tau > 0.0)) return OLB_ERR_ARG;
     if (!std::isfinite(p->ds) || !std::isfinite(p->dt) || !std::isfinite(p->tau)) return OLB_ERR_ARG;
     if (!(p->sigma >= 0.0) || !(p->b >= 0.0) || !std::isfinite(p->a) || !std::isfinite(p->sigma) ||
@@ -275,8 +278,9 @@ int olb::validate_params(const olb_params *p)
 
 static cudaError_t prepare_tile(olb_ctx *c)
 {
-    return is_fp64(c) ? prepare_fused((double *)nullptr, c->tx, c->ty, c->kp)
-                      : prepare_fused((float *)nullptr, c->tx, c->ty, c->kp);
+    const bool learned = c->p.weno_mode == OLB_WENO_LEARNED;
+    return is_fp64(c) ? prepare_fused((double *)nullptr, c->tx, c->ty, c->kp, learned)
+                      : prepare_fused((float *)nullptr, c->tx, c->ty, c->kp, learned);
 }
 
 // Default shape: 16 x 8 nodes with 2 velocity lanes (FP64) or 32 x 16
@@ -336,8 +340,10 @@ extern "C" int olb_create(const olb_params *p, void *stream, olb_ctx **out)
     for (int k = 0; k < 3; ++k) c->f[k] = ctx_alloc(c, pop);
     c->status = (int *)ctx_alloc(c, 256);
     c->stage4 = (double *)ctx_alloc(c, 4 * N * sizeof(double));
+    c->mlp = p->weno_mode == OLB_WENO_LEARNED ? (float *)ctx_alloc(c, 1348 * sizeof(float)) : nullptr;
     default_tile(c);
-    bool ok = c->f[0] && c->f[1] && c->f[2] && c->status && c->stage4;
+    bool ok = c->f[0] && c->f[1] && c->f[2] && c->status && c->stage4 &&
+              (p->weno_mode != OLB_WENO_LEARNED || c->mlp);
     cudaError_t e = cudaSuccess;
     if (ok) {
         // zero everything once so padding lanes never hold garbage
@@ -427,6 +433,7 @@ extern "C" int olb_step_async(olb_ctx *c, int nsteps)
 {
     if (!c || nsteps < 0) return OLB_ERR_ARG;
     if (!c->initialized) return OLB_ERR_STATE;
+    if (c->p.weno_mode == OLB_WENO_LEARNED && !c->mlp_set) return OLB_ERR_STATE;
     if (nsteps == 0) return OLB_OK;
     DeviceGuard dg(c->device);
     cudaError_t e = cudaSuccess;
@@ -620,5 +627,19 @@ extern "C" int olb_get_tile(olb_ctx *c, int *tx, int *ty, int *kp)
     *tx = c->tx;
     *ty = c->ty;
     *kp = c->kp;
+    return OLB_OK;
+}
+
+extern "C" int olb_set_weno_mlp(olb_ctx *c, const float *theta)
+{
+    if (!c || !theta) return OLB_ERR_ARG;
+    if (c->p.weno_mode != OLB_WENO_LEARNED) return OLB_ERR_STATE;
+    for (int k = 0; k < 1347; ++k)
+        if (!std::isfinite(theta[k])) return OLB_ERR_ARG;
+    DeviceGuard dg(c->device);
+    cudaError_t e = cudaMemcpyAsync(c->mlp, theta, 1347 * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    c->mlp_set = true;
     return OLB_OK;
 }

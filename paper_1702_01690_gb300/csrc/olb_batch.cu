@@ -102,8 +102,8 @@ static cudaError_t batch_upload(olb_batch *b)
 
 static cudaError_t batch_prepare(olb_batch *b)
 {
-    return b_fp64(b) ? prepare_fused((double *)nullptr, b->tx, b->ty, b->kp)
-                     : prepare_fused((float *)nullptr, b->tx, b->ty, b->kp);
+    return b_fp64(b) ? prepare_fused((double *)nullptr, b->tx, b->ty, b->kp, false)
+                     : prepare_fused((float *)nullptr, b->tx, b->ty, b->kp, false);
 }
 
 template <typename real>
@@ -173,6 +173,7 @@ extern "C" int olb_batch_create(const olb_params *runs, int count, void *stream,
         const int v = validate_params(&runs[r]);
         if (v != OLB_OK) return v;
         if (runs[r].precision != runs[0].precision) return OLB_ERR_ARG;
+        if (runs[r].weno_mode != OLB_WENO_JS) return OLB_ERR_ARG;
     }
     olb_batch *b = new (std::nothrow) olb_batch();
     if (!b) return OLB_ERR_NOMEM;

@@ -21,7 +21,7 @@
 //      the output buffer.  KP > 1 gives small tiles enough warps.
 #pragma once
 
-#include "olb_kernels.cuh"
+#include "olb_mlp.cuh"
 
 namespace olb {
 
@@ -79,14 +79,26 @@ __device__ __forceinline__ real sel5(const real v[NQ], int k)
     return r;
 }
 
+// Face value of one upwind-ordered stencil: Jiang-Shu weights, or the
+// learned network's (parameters in shared memory) when LEARNED.
+template <typename real, bool LEARNED>
+__device__ __forceinline__ real face_value(const float *mlp, real v0, real v1, real v2, real v3, real v4)
+{
+    if constexpr (LEARNED)
+        return weno5_learned<real>(mlp, v0, v1, v2, v3, v4);
+    else
+        return weno5(v0, v1, v2, v3, v4);
+}
+
 // One stage for the tile whose lower-left node is (x0, y0); all threads of
 // the CTA call it (it synchronises).  g and t may live in parameter space
-// (single grid) or shared memory (batch).
-template <typename real, int TX, int TY, int KP>
+// (single grid) or shared memory (batch); mlp: the learned network's
+// parameters in shared memory (LEARNED only).
+template <typename real, int TX, int TY, int KP, bool LEARNED = false>
 __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, const real *__restrict__ fs,
                                            const real *fn, real *out, int *__restrict__ status, const Geo &g,
                                            const Tab<real> &t, const int x0, const int y0, const real ca,
-                                           const real cb, const real cc)
+                                           const real cb, const real cc, const float *mlp = nullptr)
 {
     using S = FusedSmem<real, TX, TY, KP>;
     constexpr int NT = S::NT, NN = S::NN, HX = S::HX, HY = S::HY;
@@ -141,9 +153,9 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
 #pragma unroll
             for (int k = 0; k < NQ; ++k) {
                 n += sx[k];
-                jx += (double)t.R[k] * sx[k];
-                jy += (double)t.R[k] * sy[k];
-                en += (double)t.R2[k] * (sx[k] + sy[k]);
+                jx = fma((double)t.R[k], sx[k], jx);
+                jy = fma((double)t.R[k], sy[k], jy);
+                en = fma((double)t.R2[k], sx[k] + sy[k], en);
             }
         } else {
             Kahan kn{0.f, 0.f}, kx{0.f, 0.f}, ky{0.f, 0.f}, ke{0.f, 0.f};
@@ -164,7 +176,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
         }
         const double inv_n = recip_nr(n);
         const double ux = jx * inv_n, uy = jy * inv_n;
-        const double T = 0.5 * (en * inv_n - ux * ux - uy * uy);
+        const double T = 0.5 * fma(en, inv_n, -fma(ux, ux, uy * uy));
         // Delta p = n T - p^w, p^w = n T / (1 - b n) - a n^2 (Eq. vdw)
         const double nT = n * T;
         sm.n[r][c] = make_field(n, real(0));
@@ -211,8 +223,8 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 for (int k2 = 0; k2 < NQ; ++k2) {
                     const int k = NQ * k1 + k2;
                     const real a0 = sm.pop[k][r][c0], a1 = sm.pop[k][r][c0 + dc], a2 = sm.pop[k][r][c0 + 2 * dc];
-                    sm.pop[k][r][c] = m == 0 ? real(3) * a0 - real(3) * a1 + a2
-                                             : real(6) * a0 - real(8) * a1 + real(3) * a2;
+                    sm.pop[k][r][c] = m == 0 ? fma(real(3), a0 - a1, a2)
+                                             : fma(real(6), a0, fma(real(-8), a1, real(3) * a2));
                 }
             }
         }
@@ -231,8 +243,8 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 const int dc = side ? -1 : 1;
                 const real a0 = sm.pop[k][tr + 3][c0], a1 = sm.pop[k][tr + 3][c0 + dc];
                 const real a2 = sm.pop[k][tr + 3][c0 + 2 * dc];
-                const real g0 = real(3) * a0 - real(3) * a1 + a2;
-                const real g1 = real(6) * a0 - real(8) * a1 + real(3) * a2;
+                const real g0 = fma(real(3), a0 - a1, a2);
+                const real g1 = fma(real(6), a0, fma(real(-8), a1, real(3) * a2));
                 flux = t.R[k1] * weno5(a2, a1, a0, g0, g1);
             }
 #pragma unroll
@@ -275,19 +287,20 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 const int am = m < 0 ? -m : m;
                 if (grad_w(l, am) != 0.0) {
                     const real w = real(l * grad_w(l, am));
-                    ddx += w * field_diff(sm.dp[ty + cy + m][tx + cx + l], sm.dp[ty + cy + m][tx + cx - l]);
-                    ddy += w * field_diff(sm.dp[ty + cy + l][tx + cx + m], sm.dp[ty + cy - l][tx + cx + m]);
+                    ddx = fma(w, field_diff(sm.dp[ty + cy + m][tx + cx + l], sm.dp[ty + cy + m][tx + cx - l]), ddx);
+                    ddy = fma(w, field_diff(sm.dp[ty + cy + l][tx + cx + m], sm.dp[ty + cy - l][tx + cx + m]), ddy);
                 }
                 if (glap_c(am, l) != 0.0) {
                     const real w = real(glap_c(am, l));
-                    ldx += w * field_diff(sm.n[ty + cy + m][tx + cx + l], sm.n[ty + cy + m][tx + cx - l]);
-                    ldy += w * field_diff(sm.n[ty + cy + l][tx + cx + m], sm.n[ty + cy - l][tx + cx + m]);
+                    ldx = fma(w, field_diff(sm.n[ty + cy + m][tx + cx + l], sm.n[ty + cy + m][tx + cx - l]), ldx);
+                    ldy = fma(w, field_diff(sm.n[ty + cy + l][tx + cx + m], sm.n[ty + cy - l][tx + cx + m]), ldy);
                 }
             }
         nn = field_val(sm.n[ty + cy][tx + cx]);
         const real dn = real(g.inv_ds) / nn;
-        Fx = ddx * dn + real(g.sigma) * ldx * real(g.inv_ds3);
-        Fy = ddy * dn + real(g.sigma) * ldy * real(g.inv_ds3);
+        const real sg3 = real(g.sigma) * real(g.inv_ds3);
+        Fx = fma(ddx, dn, sg3 * ldx);
+        Fy = fma(ddy, dn, sg3 * ldy);
         eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], gx);
         eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gy);
         if constexpr (KP > 1) {
@@ -322,8 +335,9 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 if (y0 + r < g.ny && x0 + c <= g.nx) {
                     // face at x = x0 + c: nodes x0+c-3 .. x0+c+2 are columns c+1 .. c+6
                     const real *row = &sm.pop[k][3 + r][0];
-                    sm.fx[sub][r][c] = (k1 > 2) ? weno5(row[c + 1], row[c + 2], row[c + 3], row[c + 4], row[c + 5])
-                                                : weno5(row[c + 6], row[c + 5], row[c + 4], row[c + 3], row[c + 2]);
+                    sm.fx[sub][r][c] =
+                        (k1 > 2) ? face_value<real, LEARNED>(mlp, row[c + 1], row[c + 2], row[c + 3], row[c + 4], row[c + 5])
+                                 : face_value<real, LEARNED>(mlp, row[c + 6], row[c + 5], row[c + 4], row[c + 3], row[c + 2]);
                 }
             } else {
                 if (k2 == 2) continue;
@@ -333,10 +347,10 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                     // face at y = y0 + r: rows y0+r-3 .. y0+r+2 are rows r .. r+5
                     const int cc4 = 4 + c;
                     const real(*P)[HX] = sm.pop[k];
-                    sm.fy[sub][r][c] = (k2 > 2) ? weno5(P[r][cc4], P[r + 1][cc4], P[r + 2][cc4], P[r + 3][cc4],
-                                                        P[r + 4][cc4])
-                                                : weno5(P[r + 5][cc4], P[r + 4][cc4], P[r + 3][cc4], P[r + 2][cc4],
-                                                        P[r + 1][cc4]);
+                    sm.fy[sub][r][c] = (k2 > 2) ? face_value<real, LEARNED>(mlp, P[r][cc4], P[r + 1][cc4], P[r + 2][cc4],
+                                                                            P[r + 3][cc4], P[r + 4][cc4])
+                                                : face_value<real, LEARNED>(mlp, P[r + 5][cc4], P[r + 4][cc4],
+                                                                            P[r + 3][cc4], P[r + 2][cc4], P[r + 1][cc4]);
                 }
             }
         }
@@ -348,8 +362,8 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             real dx = 0, dy = 0;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                dx += t.D[k1][q] * sm.pop[NQ * q + k2][r][c];
-                dy += t.D[k2][q] * sm.pop[NQ * k1 + q][r][c];
+                dx = fma(t.D[k1][q], sm.pop[NQ * q + k2][r][c], dx);
+                dy = fma(t.D[k2][q], sm.pop[NQ * k1 + q][r][c], dy);
             }
             const real f = sm.pop[k][r][c];
             real feq, fxv, fyv;
@@ -363,25 +377,46 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 fyv = Fy;
             }
             real adv = 0;
-            if (k1 != 2) adv += t.R[k1] * (sm.fx[lane_k][ty][tx + 1] - sm.fx[lane_k][ty][tx]);
-            if (k2 != 2) adv += t.R[k2] * (sm.fy[lane_k][ty + 1][tx] - sm.fy[lane_k][ty][tx]);
-            const real Lloc = -(fxv * dx + fyv * dy) - (f - feq) * itau;
-            real v = cb * f + cc * Lloc - cadv * adv;
-            if (ca != real(0)) v += ca * fn[k * g.plane + o];
+            if (k1 != 2) adv = t.R[k1] * (sm.fx[lane_k][ty][tx + 1] - sm.fx[lane_k][ty][tx]);
+            if (k2 != 2) adv = fma(t.R[k2], sm.fy[lane_k][ty + 1][tx] - sm.fy[lane_k][ty][tx], adv);
+            const real Lloc = -fma(fxv, dx, fyv * dy) - (f - feq) * itau;
+            real v = fma(cb, f, fma(cc, Lloc, -cadv * adv));
+            if (ca != real(0)) v = fma(ca, fn[k * g.plane + o], v);
             out[k * g.plane + o] = v;
         }
     }
 }
 
-// Single grid: one CTA per tile.
+// Shared memory of the single-grid kernel: the tile staging, then (learned
+// weights only) the network's parameters at a 16-byte aligned offset.
 template <typename real, int TX, int TY, int KP>
+constexpr size_t mlp_offset()
+{
+    return (sizeof(FusedSmem<real, TX, TY, KP>) + 15) / 16 * 16;
+}
+template <typename real, int TX, int TY, int KP, bool LEARNED>
+constexpr size_t fused_smem_bytes()
+{
+    return LEARNED ? mlp_offset<real, TX, TY, KP>() + (MLP_P + 1) * sizeof(float) : sizeof(FusedSmem<real, TX, TY, KP>);
+}
+
+// Single grid: one CTA per tile.
+template <typename real, int TX, int TY, int KP, bool LEARNED>
 __global__ void __launch_bounds__(TX *TY *KP)
 k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
-        const __grid_constant__ Geo g, const __grid_constant__ Tab<real> t, real ca, real cb, real cc)
+        const __grid_constant__ Geo g, const __grid_constant__ Tab<real> t, real ca, real cb, real cc,
+        const float *__restrict__ mlp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<FusedSmem<real, TX, TY, KP> *>(smem_raw);
-    stage_tile<real, TX, TY, KP>(sm, fs, fn, out, status, g, t, blockIdx.x * TX, blockIdx.y * TY, ca, cb, cc);
+    float *mlp_sm = nullptr;
+    if constexpr (LEARNED) {
+        mlp_sm = reinterpret_cast<float *>(smem_raw + mlp_offset<real, TX, TY, KP>());
+        for (int p = threadIdx.x; p < MLP_P; p += blockDim.x) mlp_sm[p] = __ldg(mlp + p);
+        // made visible by the first barrier inside stage_tile
+    }
+    stage_tile<real, TX, TY, KP, LEARNED>(sm, fs, fn, out, status, g, t, blockIdx.x * TX, blockIdx.y * TY, ca, cb, cc,
+                                          mlp_sm);
 }
 
 // Batch of independent runs (uneven grid sizes, own parameters): a
@@ -433,14 +468,25 @@ k_fused_batch(const real *__restrict__ fs, const real *fn, real *out, int *__res
     }
 }
 
-template <typename real, int TX, int TY, int KP>
+template <typename real, int TX, int TY, int KP, bool LEARNED = false>
 cudaError_t fused_prepare_one()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_fused<real, TX, TY, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(FusedSmem<real, TX, TY, KP>));
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaFuncSetAttribute(k_fused<real, TX, TY, KP, LEARNED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fused_smem_bytes<real, TX, TY, KP, LEARNED>());
+    if (e != cudaSuccess || LEARNED) return e;
     return cudaFuncSetAttribute(k_fused_batch<real, TX, TY, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(FusedSmem<real, TX, TY, KP>));
+}
+
+template <typename real, int TX, int TY, int KP, bool LEARNED = false>
+cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *status, const Geo &g,
+                             const Tab<real> &t, StageCoef c, const float *mlp, cudaStream_t s)
+{
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
+    k_fused<real, TX, TY, KP, LEARNED><<<grid, TX * TY * KP, fused_smem_bytes<real, TX, TY, KP, LEARNED>(), s>>>(
+        fs, fn, out, status, g, t, (real)c.ca, (real)c.cb, (real)c.cc, mlp);
+    return cudaGetLastError();
 }
 
 template <typename real, int TX, int TY, int KP>
@@ -480,23 +526,33 @@ cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *sta
 // advanced at once (TX*TY*KP threads).  Must match TILE_X/TILE_Y/TILE_K in
 // olb_internal.cuh.
 #define OLB_FUSED_SHAPE_CASES(real, DO) DO(real, 8, 8, 4) DO(real, 16, 8, 2) DO(real, 16, 8, 1) DO(real, 32, 8, 1) DO(real, 32, 16, 1)
+// Shapes with a learned-weights instance (the default shapes of both precisions).
+#define OLB_FUSED_LEARNED_CASES(real, DO) DO(real, 8, 8, 4) DO(real, 16, 8, 2) DO(real, 32, 16, 1)
 #define OLB_FUSED_PREP_CASE(real, A, B, C) \
-    if (tx == A && ty == B && kp == C) return fused_prepare_one<real, A, B, C>();
+    if (!learned && tx == A && ty == B && kp == C) return fused_prepare_one<real, A, B, C>();
+#define OLB_FUSED_PREP_LEARNED(real, A, B, C) \
+    if (learned && tx == A && ty == B && kp == C) return fused_prepare_one<real, A, B, C, true>();
 #define OLB_FUSED_LAUNCH_CASE(real, A, B, C) \
-    if (tx == A && ty == B && kp == C) return fused_launch_one<real, A, B, C>(fs, fn, out, status, g, t, c, s);
+    if (!mlp && tx == A && ty == B && kp == C) return fused_launch_one<real, A, B, C>(fs, fn, out, status, g, t, c, mlp, s);
+#define OLB_FUSED_LAUNCH_LEARNED(real, A, B, C)                 \
+    if (mlp && tx == A && ty == B && kp == C)                   \
+        return fused_launch_one<real, A, B, C, true>(fs, fn, out, status, g, t, c, mlp, s);
 #define OLB_FUSED_BATCH_CASE(real, A, B, C)                                                                  \
     if (tx == A && ty == B && kp == C)                                                                       \
         return fused_batch_launch_one<real, A, B, C>(fs, fn, out, status, runs, tile_start, nruns, total, c, s);
 #define OLB_DEFINE_FUSED(real)                                                                                \
-    cudaError_t prepare_fused(real *, int tx, int ty, int kp)                                                 \
+    cudaError_t prepare_fused(real *, int tx, int ty, int kp, bool learned)                                   \
     {                                                                                                         \
         OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_PREP_CASE)                                                      \
+        OLB_FUSED_LEARNED_CASES(real, OLB_FUSED_PREP_LEARNED)                                                 \
         return cudaErrorInvalidValue;                                                                         \
     }                                                                                                         \
     cudaError_t launch_fused(const real *fs, const real *fn, real *out, int *status, const Geo &g,            \
-                             const Tab<real> &t, StageCoef c, int tx, int ty, int kp, cudaStream_t s)         \
+                             const Tab<real> &t, StageCoef c, int tx, int ty, int kp, const float *mlp,       \
+                             cudaStream_t s)                                                                  \
     {                                                                                                         \
         OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_LAUNCH_CASE)                                                    \
+        OLB_FUSED_LEARNED_CASES(real, OLB_FUSED_LAUNCH_LEARNED)                                               \
         return cudaErrorInvalidValue;                                                                         \
     }                                                                                                         \
     cudaError_t launch_fused_batch(const real *fs, const real *fn, real *out, int *status, const void *runs,  \

@@ -61,9 +61,10 @@ struct StageCoef {
 // Launchers, one set per precision (olb_fp64.cu, olb_fp32.cu).  Output
 // pointers of launch_moments_out may be NULL to skip a field.
 #define OLB_DECLARE_LAUNCHERS(real)                                                                    \
-    cudaError_t prepare_fused(real *, int tx, int ty, int kp);                                         \
+    cudaError_t prepare_fused(real *, int tx, int ty, int kp, bool learned);                           \
     cudaError_t launch_fused(const real *fs, const real *fn, real *out, int *status, const Geo &g,     \
-                             const Tab<real> &t, StageCoef c, int tx, int ty, int kp, cudaStream_t s); \
+                             const Tab<real> &t, StageCoef c, int tx, int ty, int kp,                  \
+                             const float *mlp, cudaStream_t s);                                        \
     cudaError_t launch_fused_batch(const real *fs, const real *fn, real *out, int *status,             \
                                    const void *runs, const int *tile_start, int nruns, int total,      \
                                    StageCoef c, int tx, int ty, int kp, cudaStream_t s);               \

@@ -157,11 +157,11 @@ __device__ __forceinline__ void eq_factors(const Tab<real> &t, real u, real T, r
     const real u2 = u * u;
     const real c1 = u;
     const real c2 = real(0.5) * (u2 + th);
-    const real c3 = u * (u2 * real(1.0 / 6.0) + real(0.5) * th);
-    const real c4 = u2 * u2 * real(1.0 / 24.0) + real(0.25) * th * u2 + real(0.125) * th * th;
+    const real c3 = u * fma(u2, real(1.0 / 6.0), real(0.5) * th);
+    const real c4 = fma(u2 * u2, real(1.0 / 24.0), fma(real(0.25) * th, u2, real(0.125) * th * th));
 #pragma unroll
     for (int k = 0; k < NQ; ++k)
-        g[k] = t.wHe[k][0] + t.wHe[k][1] * c1 + t.wHe[k][2] * c2 + t.wHe[k][3] * c3 + t.wHe[k][4] * c4;
+        g[k] = fma(t.wHe[k][4], c4, fma(t.wHe[k][3], c3, fma(t.wHe[k][2], c2, fma(t.wHe[k][1], c1, t.wHe[k][0]))));
 }
 
 // Kahan-compensated accumulation (FP32 variant).
@@ -205,9 +205,9 @@ __device__ __forceinline__ void node_sums<double>(const double *__restrict__ f, 
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
         n += sx[k];
-        jx += t.R[k] * sx[k];
-        jy += t.R[k] * sy[k];
-        e += t.R2[k] * (sx[k] + sy[k]);
+        jx = fma(t.R[k], sx[k], jx);
+        jy = fma(t.R[k], sy[k], jy);
+        e = fma(t.R2[k], sx[k] + sy[k], e);
     }
 }
 
@@ -267,7 +267,7 @@ __global__ void k_moments_out(const real *__restrict__ f, double *__restrict__ o
     if (on) on[idx] = n;
     if (oux) oux[idx] = ux;
     if (ouy) ouy[idx] = uy;
-    if (oT) oT[idx] = 0.5 * (e / n - ux * ux - uy * uy);
+    if (oT) oT[idx] = 0.5 * (e / n - fma(ux, ux, uy * uy));
 }
 
 template <typename real>

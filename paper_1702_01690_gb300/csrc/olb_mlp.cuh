@@ -1,0 +1,93 @@
+// olb_mlp.cuh -- the learned WENO-5 weight network on the device.
+//
+// A 5-32-32-3 MLP (tanh, tanh, softmax) maps the normalised stencil
+// x = (v - mean v) / (max v - min v) of an interface to three convex weights
+// that replace the Jiang-Shu weights of Eq. weno5_omega.  Parameters, 1347
+// floats: W1 [32][5], b1 [32], W2 [32][32], b2 [32], W3 [3][32], b3 [3]
+// (row-major, concatenated).
+#pragma once
+
+#include "olb_kernels.cuh"
+
+namespace olb {
+
+constexpr int MLP_IN = 5, MLP_H = 32, MLP_OUT = 3;
+constexpr int MLP_W1 = 0, MLP_B1 = 160, MLP_W2 = 192, MLP_B2 = 1216, MLP_W3 = 1248, MLP_B3 = 1344;
+constexpr int MLP_P = 1347;
+
+// Weights of one stencil; th points to the parameters (shared memory in the
+// stage kernel).  x: normalised stencil.
+__device__ __forceinline__ void mlp_weights(const float *__restrict__ th, const float x[MLP_IN], float w[MLP_OUT])
+{
+    float h1[MLP_H];
+#pragma unroll
+    for (int j = 0; j < MLP_H; ++j) {
+        float a = th[MLP_B1 + j];
+#pragma unroll
+        for (int q = 0; q < MLP_IN; ++q) a = fmaf(th[MLP_W1 + j * MLP_IN + q], x[q], a);
+        h1[j] = tanhf(a);
+    }
+    float z0 = th[MLP_B3 + 0], z1 = th[MLP_B3 + 1], z2 = th[MLP_B3 + 2];
+#pragma unroll 4
+    for (int j = 0; j < MLP_H; ++j) {
+        const float4 *row = reinterpret_cast<const float4 *>(th + MLP_W2 + j * MLP_H);
+        float a = th[MLP_B2 + j];
+#pragma unroll
+        for (int k4 = 0; k4 < MLP_H / 4; ++k4) {
+            const float4 r = row[k4];
+            a = fmaf(r.x, h1[4 * k4 + 0], a);
+            a = fmaf(r.y, h1[4 * k4 + 1], a);
+            a = fmaf(r.z, h1[4 * k4 + 2], a);
+            a = fmaf(r.w, h1[4 * k4 + 3], a);
+        }
+        const float h2 = tanhf(a);
+        z0 = fmaf(th[MLP_W3 + 0 * MLP_H + j], h2, z0);
+        z1 = fmaf(th[MLP_W3 + 1 * MLP_H + j], h2, z1);
+        z2 = fmaf(th[MLP_W3 + 2 * MLP_H + j], h2, z2);
+    }
+    const float zm = fmaxf(z0, fmaxf(z1, z2));
+    const float e0 = expf(z0 - zm), e1 = expf(z1 - zm), e2 = expf(z2 - zm);
+    const float inv = 1.0f / (e0 + e1 + e2);
+    w[0] = e0 * inv;
+    w[1] = e1 * inv;
+    w[2] = e2 * inv;
+}
+
+// Learned WENO-5 interface value (without p/m) of the upwind-ordered stencil:
+// where any smoothness indicator vanishes the Jiang-Shu weights with Table
+// tab:weno apply (constant ghost layers keep their exact flux); otherwise
+// v2 + sum_q w_q G_q with the network's weights.  The network runs in FP32;
+// the candidates are combined in the population precision.
+template <typename real>
+__device__ __forceinline__ real weno5_learned(const float *__restrict__ th, real v0, real v1, real v2, real v3,
+                                              real v4)
+{
+    const real d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
+    const real a1 = d12 - d01, b1 = fma(real(3), d12, -d01);
+    const real a2 = d23 - d12, b2 = d12 + d23;
+    const real a3 = d34 - d23, b3 = fma(real(-3), d23, d34);
+    const bool zero = (a1 == real(0) && b1 == real(0)) || (a2 == real(0) && b2 == real(0)) ||
+                      (a3 == real(0) && b3 == real(0));
+    if (zero) return weno5(v0, v1, v2, v3, v4);
+    real mx = v0, mn = v0;
+    mx = v1 > mx ? v1 : mx;
+    mn = v1 < mn ? v1 : mn;
+    mx = v2 > mx ? v2 : mx;
+    mn = v2 < mn ? v2 : mn;
+    mx = v3 > mx ? v3 : mx;
+    mn = v3 < mn ? v3 : mn;
+    mx = v4 > mx ? v4 : mx;
+    mn = v4 < mn ? v4 : mn;
+    const real mean = (v0 + v1 + v2 + v3 + v4) * real(0.2);
+    const real ir = real(1) / (mx - mn);
+    const float x[MLP_IN] = {(float)((v0 - mean) * ir), (float)((v1 - mean) * ir), (float)((v2 - mean) * ir),
+                             (float)((v3 - mean) * ir), (float)((v4 - mean) * ir)};
+    float w[MLP_OUT];
+    mlp_weights(th, x, w);
+    const real G1 = fma(real(5.0 / 6.0), d12, real(-1.0 / 3.0) * d01);
+    const real G2 = fma(real(1.0 / 3.0), d23, real(1.0 / 6.0) * d12);
+    const real G3 = fma(real(2.0 / 3.0), d23, real(-1.0 / 6.0) * d34);
+    return fma((real)w[0], G1, fma((real)w[1], G2, fma((real)w[2], G3, v2)));
+}
+
+}  // namespace olb

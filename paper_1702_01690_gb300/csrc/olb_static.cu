@@ -117,7 +117,7 @@ extern "C" int olb_step_static(const olb_params *p, void *stream, double *f, int
     // CTAs, else 8 x 8 nodes with 4 lanes
     const long long ctas = (long long)((g.nx + 15) / 16) * ((g.ny + 7) / 8);
     const int tx = ctas >= 2 * 152 ? 16 : 8, ty = 8, kp = ctas >= 2 * 152 ? 2 : 4;
-    cudaError_t e = prepare_fused((double *)nullptr, tx, ty, kp);
+    cudaError_t e = prepare_fused((double *)nullptr, tx, ty, kp, false);
     // the scratch keeps the previous call's contents: the status word must start at zero
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s);
     const double dt = p->dt;
@@ -126,7 +126,7 @@ extern "C" int olb_step_static(const olb_params *p, void *stream, double *f, int
     double *dst[3] = {f1, f2, f};
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
         for (int st = 0; st < 3 && e == cudaSuccess; ++st)
-            e = launch_fused(src[st], f, dst[st], status, g, tab, coef[st], tx, ty, kp, s);
+            e = launch_fused(src[st], f, dst[st], status, g, tab, coef[st], tx, ty, kp, nullptr, s);
     int hstatus = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -1,0 +1,187 @@
+"""Training data and training of the learned WENO-5 weights.
+
+The network (see olb_mlp_* in include/olb.h) replaces the Jiang-Shu weights
+of Eq. weno5_omega.  Its training data come from this solver:
+
+* fine-grid fields: populations of periodic runs (Laplace drops, waves,
+  band-limited noise) advanced a few steps by the library's FP64 path;
+* coarse stencils: every `ratio`-th node of a grid line, i.e. the five
+  values the coarse scheme (spacing h = ratio ds) sees at an interface, in
+  both upwind orientations;
+* targets: the value a finite-difference WENO flux should take at the
+  interface, h(x_{i+1/2}) of the function h whose cell averages (width h) are
+  the point values f: h = f - h^2/24 f'' + 7 h^4/5760 f'''' + O(h^6) (the
+  inverse of the cell-average operator), with f'' and f'''' from central
+  differences of orders 6 and 4 on the fine line at the interface, which is a
+  fine node when ratio is even.
+
+Stencils whose smoothness indicators vanish (the network is not used there:
+Table tab:weno applies) and flat stencils are dropped.  Inputs are
+normalised as x = (v - mean)/(max - min); the candidate offsets G_q (Eq.
+weno5_flux minus the centre value) and the target offset are divided by the
+same range.  Training runs on the GPU through olb_mlp_train.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import inputs
+
+
+def _js_sigma_zero(V):
+    """Rows of stencils V [S][5] with a vanishing smoothness indicator."""
+    d = np.diff(V, axis=1)
+    a1, b1 = d[:, 1] - d[:, 0], 3 * d[:, 1] - d[:, 0]
+    a2, b2 = d[:, 2] - d[:, 1], d[:, 1] + d[:, 2]
+    a3, b3 = d[:, 3] - d[:, 2], d[:, 3] - 3 * d[:, 2]
+    return ((a1 == 0) & (b1 == 0)) | ((a2 == 0) & (b2 == 0)) | ((a3 == 0) & (b3 == 0))
+
+
+def candidate_offsets(V):
+    """G_q = F^q - v2 (Eq. weno5_flux) of upwind-ordered stencils V [S][5]."""
+    v0, v1, v2, v3, v4 = np.asarray(V, dtype=np.float64).T
+    return np.stack([(2 * v0 - 7 * v1 + 5 * v2) / 6, (-v1 - v2 + 2 * v3) / 6, (-4 * v2 + 5 * v3 - v4) / 6], axis=1)
+
+
+def line_samples(line, ratio: int = 4):
+    """Stencils and targets from one periodic fine line (ratio even)."""
+    f = np.asarray(line, dtype=np.float64)
+    L = f.size
+    h = float(ratio)  # in fine-node units; targets are scale-free below
+    # derivatives at every fine node (periodic), fine spacing 1
+    s = lambda k: np.roll(f, -k)
+    d2 = (s(3) + s(-3)) / 90 - 3 * (s(2) + s(-2)) / 20 + 1.5 * (s(1) + s(-1)) - 49 / 18 * f
+    d4 = (-(s(3) + s(-3)) + 12 * (s(2) + s(-2)) - 39 * (s(1) + s(-1)) + 56 * f) / 6
+    target = f - h * h / 24 * d2 + 7 * h ** 4 / 5760 * d4
+    Vs, Ts = [], []
+    for o in range(ratio):
+        idx = (o + ratio * np.arange(L // ratio)) % L
+        c = f[idx]
+        n = c.size
+        if n < 6:
+            continue
+        i = np.arange(n)
+        face = (idx + ratio // 2) % L                    # fine node at x_{i+1/2}
+        # p > 0: c_{i-2} .. c_{i+2};  p < 0: c_{i+3} .. c_{i-1}
+        pos = np.stack([c[(i + k) % n] for k in (-2, -1, 0, 1, 2)], axis=1)
+        neg = np.stack([c[(i + k) % n] for k in (3, 2, 1, 0, -1)], axis=1)
+        Vs += [pos, neg]
+        Ts += [target[face], target[face]]
+    return np.concatenate(Vs), np.concatenate(Ts)
+
+
+def normalised_samples(V, t):
+    """x, Gn, tn (float32) for stencils V and targets t; drops stencils the
+    network never sees (vanishing indicators, zero range)."""
+    V = np.asarray(V, dtype=np.float64)
+    t = np.asarray(t, dtype=np.float64)
+    r = V.max(axis=1) - V.min(axis=1)
+    keep = (~_js_sigma_zero(V)) & (r > 1e-13 * np.maximum(np.abs(V).max(axis=1), 1e-300))
+    V, t, r = V[keep], t[keep], r[keep]
+    x = (V - V.mean(axis=1, keepdims=True)) / r[:, None]
+    Gn = candidate_offsets(V) / r[:, None]
+    tn = (t - V[:, 2]) / r
+    return (x.astype(np.float32), Gn.astype(np.float32), tn.astype(np.float32)), (V, t)
+
+
+def default_sources(scale: int = 1):
+    """Periodic fine-grid runs used for training (steps to advance first)."""
+    out = []
+    n = 512 * scale
+    for R in (0.1, 0.2, 0.3):
+        p, f = inputs.laplace(n, R=R, steps=4)
+        out.append((p, f, 4))
+    ds = 1.0 / (256 * scale)
+    for amp in (0.05, 0.2):
+        p = inputs.RunParams(nx=256 * scale, ny=256 * scale, ds=ds, dt=inputs.stable_dt(ds), tau=0.01)
+        out.append((p, inputs.shear_wave(p.nx, p.ny, ds, 1.0, 0.9, amp), 4))
+        out.append((p, inputs.longitudinal_wave(p.nx, p.ny, ds, 1.0, 0.9, amp), 4))
+    ds = 1.0 / (512 * scale)
+    p = inputs.RunParams(nx=512 * scale, ny=64, ds=ds, dt=inputs.stable_dt(ds, n_max=1.1), tau=0.005)
+    n0 = 1.0 + 0.05 * inputs.band_limited_noise(p.nx, p.ny, inputs.SEED_BASE + 7, 8)
+    z = np.zeros_like(n0)
+    out.append((p, (n0, z, z.copy(), np.ones_like(n0)), 4))
+    return out
+
+
+def harvest(sources=None, ratio: int = 4, row_stride: int = 16, velocities=None):
+    """Raw stencils V [S][5] and targets t [S] from solver runs (FP64 path)."""
+    from . import olb
+    if sources is None:
+        sources = default_sources()
+    moving = velocities if velocities is not None else [k for k in range(25) if k // 5 != 2]
+    Vs, Ts = [], []
+    for p, fields, steps in sources:
+        ctx = olb.create(p)
+        ctx.init_fields(*fields)
+        ctx.step(steps)
+        f = ctx.get_populations()
+        ctx.close()
+        for k in moving:
+            for j in range(0, p.ny, row_stride):  # x lines (periodic runs only)
+                V, t = line_samples(f[k, j, :], ratio)
+                Vs.append(V)
+                Ts.append(t)
+    return np.concatenate(Vs), np.concatenate(Ts)
+
+
+def train(x, Gn, tn, epochs: int = 40, batch: int = 4096, lr: float = 2e-3, seed: int = 0):
+    """Glorot-initialised network trained on the GPU; returns (theta as a
+    numpy float32 array, loss history)."""
+    import torch
+    from . import olb
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(len(tn))
+    x, Gn, tn = x[perm], Gn[perm], tn[perm]
+    sizes = [(32, 5), (32,), (32, 32), (32,), (3, 32), (3,)]
+    parts = []
+    for shp in sizes:
+        if len(shp) == 2:
+            lim = np.sqrt(6.0 / (shp[0] + shp[1]))
+            parts.append(rng.uniform(-lim, lim, shp).ravel())
+        else:
+            parts.append(np.zeros(shp))
+    theta = torch.tensor(np.concatenate(parts), dtype=torch.float32, device="cuda")
+    hist = olb.mlp_train(theta, torch.from_numpy(x).cuda(), torch.from_numpy(Gn).cuda(),
+                         torch.from_numpy(tn).cuda(), epochs, batch, lr)
+    return theta.cpu().numpy(), hist
+
+
+def js_face_values(V):
+    """Jiang-Shu WENO-5 interface values (Eq. weno5_omega with eps = 0 and
+    Table tab:weno) of stencils V [S][5], for comparisons on the host."""
+    V = np.asarray(V, dtype=np.float64)
+    v0, v1, v2, v3, v4 = V.T
+    s1 = 13 / 12 * (v0 - 2 * v1 + v2) ** 2 + 0.25 * (v0 - 4 * v1 + 3 * v2) ** 2
+    s2 = 13 / 12 * (v1 - 2 * v2 + v3) ** 2 + 0.25 * (v1 - v3) ** 2
+    s3 = 13 / 12 * (v2 - 2 * v3 + v4) ** 2 + 0.25 * (3 * v2 - 4 * v3 + v4) ** 2
+    S = np.stack([s1, s2, s3], axis=1)
+    d = np.array([0.1, 0.6, 0.3])
+    zero = S == 0
+    anyz = zero.any(axis=1)
+    smin = np.where(anyz, 1.0, S.min(axis=1))
+    wt = np.where(anyz[:, None], d * zero, d * (smin[:, None] / np.where(S == 0, 1.0, S)) ** 2)
+    wt = wt / wt.sum(axis=1, keepdims=True)
+    return v2 + (wt * candidate_offsets(V)).sum(axis=1)
+
+
+def learned_face_values(theta, V):
+    """Interface values with the network's weights (FP64 evaluation on the
+    host, Table tab:weno where an indicator vanishes)."""
+    V = np.asarray(V, dtype=np.float64)
+    th = np.asarray(theta, dtype=np.float64)
+    W1, b1 = th[:160].reshape(32, 5), th[160:192]
+    W2, b2 = th[192:1216].reshape(32, 32), th[1216:1248]
+    W3, b3 = th[1248:1344].reshape(3, 32), th[1344:1347]
+    r = V.max(axis=1) - V.min(axis=1)
+    rs = np.where(r > 0, r, 1.0)
+    x = (V - V.mean(axis=1, keepdims=True)) / rs[:, None]
+    z = np.tanh(np.tanh(x @ W1.T + b1) @ W2.T + b2) @ W3.T + b3
+    z -= z.max(axis=1, keepdims=True)
+    w = np.exp(z)
+    w /= w.sum(axis=1, keepdims=True)
+    out = V[:, 2] + (w * candidate_offsets(V)).sum(axis=1)
+    zero = _js_sigma_zero(V)
+    if zero.any():
+        out[zero] = js_face_values(V[zero])
+    return out

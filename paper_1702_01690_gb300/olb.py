@@ -24,7 +24,8 @@ OK = 0
 ERR_ARG, ERR_CFL, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE, ERR_NOMEM = -1, -2, -3, -4, -5, -6, -7
 SIDE_PERIODIC, SIDE_DIFFUSE = 0, 1
 FP64, FP32_KAHAN = 0, 1
-WENO_JS = 0
+WENO_JS, WENO_LEARNED = 0, 1
+MLP_PARAMS = 1347
 
 SYMBOLS = ("olb_set_allocator", "olb_create", "olb_destroy", "olb_init_fields",
            "olb_init_fields_device", "olb_step", "olb_step_async", "olb_get_status",
@@ -33,7 +34,8 @@ SYMBOLS = ("olb_set_allocator", "olb_create", "olb_destroy", "olb_init_fields",
            "olb_batch_create", "olb_batch_destroy", "olb_batch_init_fields", "olb_batch_step",
            "olb_batch_step_async", "olb_batch_get_status", "olb_batch_moments",
            "olb_batch_get_populations", "olb_batch_set_tile", "olb_batch_get_tile",
-           "olb_batch_autotune", "olb_batch_profile")
+           "olb_batch_autotune", "olb_batch_profile", "olb_mlp_forward", "olb_mlp_grad",
+           "olb_mlp_train", "olb_set_weno_mlp")
 
 
 class Params(ctypes.Structure):
@@ -101,6 +103,15 @@ _lib.olb_batch_autotune.argtypes = [_VP, ctypes.c_int, _VP, _VP, _VP]
 _lib.olb_batch_autotune.restype = ctypes.c_int
 _lib.olb_batch_profile.argtypes = [_VP, ctypes.c_int, _VP]
 _lib.olb_batch_profile.restype = ctypes.c_int
+_lib.olb_mlp_forward.argtypes = [_VP, _VP, ctypes.c_int, _VP, _VP]
+_lib.olb_mlp_forward.restype = ctypes.c_int
+_lib.olb_mlp_grad.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP]
+_lib.olb_mlp_grad.restype = ctypes.c_int
+_lib.olb_mlp_train.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                               _VP, _VP]
+_lib.olb_mlp_train.restype = ctypes.c_int
+_lib.olb_set_weno_mlp.argtypes = [_VP, _VP]
+_lib.olb_set_weno_mlp.restype = ctypes.c_int
 _lib.olb_status_string.argtypes = [ctypes.c_int]
 _lib.olb_status_string.restype = ctypes.c_char_p
 
@@ -166,7 +177,7 @@ def _dev_ptr(t):
     return _VP(t.data_ptr())
 
 
-def params_from(run, precision: int = FP64) -> Params:
+def params_from(run, precision: int = FP64, weno_mode: int = WENO_JS) -> Params:
     """Params from any object with the fields of inputs.RunParams."""
     p = Params()
     p.nx, p.ny = int(run.nx), int(run.ny)
@@ -176,7 +187,7 @@ def params_from(run, precision: int = FP64) -> Params:
     p.uw[0], p.uw[1] = float(run.uw[0]), float(run.uw[1])
     p.side_x, p.side_y = int(run.side_x), int(run.side_y)
     p.precision = int(precision)
-    p.weno_mode = WENO_JS
+    p.weno_mode = int(weno_mode)
     return p
 
 
@@ -268,13 +279,64 @@ class Context:
         _check(_lib.olb_get_populations(self._h, _host_ptr(out)), "olb_get_populations")
         return out
 
+    def set_weno_mlp(self, theta) -> None:
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32).reshape(MLP_PARAMS))
+        _check(_lib.olb_set_weno_mlp(self._h, th.ctypes.data_as(_VP)), "olb_set_weno_mlp")
+
     def set_populations(self, f) -> None:
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(25, self.ny, self.nx)
         _check(_lib.olb_set_populations(self._h, _host_ptr(f)), "olb_set_populations")
 
 
-def create(run, precision: int = FP64, stream=None) -> Context:
-    return Context(params_from(run, precision), stream)
+def create(run, precision: int = FP64, stream=None, weno_mode: int = WENO_JS) -> Context:
+    return Context(params_from(run, precision, weno_mode), stream)
+
+
+# ------------------------------------------------------------ learned weights
+def _f32_dev(t, shape=None):
+    import torch
+    t = torch.as_tensor(t, dtype=torch.float32, device="cuda").contiguous()
+    if shape is not None:
+        assert tuple(t.shape) == tuple(shape), (t.shape, shape)
+    return t
+
+
+def mlp_forward(theta, x):
+    """Weights [n][3] of normalised stencils x [n][5] (CUDA tensors)."""
+    import torch
+    theta = _f32_dev(theta, (MLP_PARAMS,))
+    x = _f32_dev(x)
+    w = torch.empty((x.shape[0], 3), dtype=torch.float32, device="cuda")
+    _check(_lib.olb_mlp_forward(_VP(theta.data_ptr()), _VP(x.data_ptr()), int(x.shape[0]), _VP(w.data_ptr()),
+                                _VP(torch.cuda.current_stream().cuda_stream)), "olb_mlp_forward")
+    return w
+
+
+def mlp_grad(theta, x, gn, tn):
+    """(mean loss, gradient) on the device for samples x [n][5], gn [n][3], tn [n]."""
+    import torch
+    theta = _f32_dev(theta, (MLP_PARAMS,))
+    x, gn, tn = _f32_dev(x), _f32_dev(gn), _f32_dev(tn)
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    _check(_lib.olb_mlp_grad(_VP(theta.data_ptr()), _VP(x.data_ptr()), _VP(gn.data_ptr()), _VP(tn.data_ptr()),
+                             int(x.shape[0]), _VP(grad.data_ptr()), _VP(loss.data_ptr()),
+                             _VP(torch.cuda.current_stream().cuda_stream)), "olb_mlp_grad")
+    return float(loss.item()), grad
+
+
+def mlp_train(theta, x, gn, tn, epochs: int, batch: int = 4096, lr: float = 1e-3):
+    """Train theta (CUDA float32 tensor, updated in place); returns the loss
+    history per epoch."""
+    import torch
+    assert theta.is_cuda and theta.dtype == torch.float32 and theta.numel() == MLP_PARAMS
+    x, gn, tn = _f32_dev(x), _f32_dev(gn), _f32_dev(tn)
+    hist = np.zeros(int(epochs), dtype=np.float32)
+    _check(_lib.olb_mlp_train(_VP(theta.data_ptr()), _VP(x.data_ptr()), _VP(gn.data_ptr()), _VP(tn.data_ptr()),
+                              int(x.shape[0]), int(epochs), int(batch), ctypes.c_float(lr),
+                              _VP(torch.cuda.current_stream().cuda_stream), hist.ctypes.data_as(_VP)),
+           "olb_mlp_train")
+    return hist
 
 
 class Batch:

@@ -1,0 +1,76 @@
+"""Pins of the FP64 reference of the learned WENO weight network (CPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+
+
+def data(S=64, seed=0):
+    rng = np.random.default_rng(seed)
+    V = rng.normal(size=(S, 5)).cumsum(axis=1)
+    X, r = mlp.normalise(V)
+    G = mlp.candidates(V) / r[:, None]
+    t = rng.normal(scale=0.3, size=S)
+    return V, X, G, t
+
+
+def test_parameter_count():
+    assert mlp.N_PARAMS == 5 * 32 + 32 + 32 * 32 + 32 + 3 * 32 + 3 == 1347
+
+
+def test_grad_matches_central_differences():
+    theta = mlp.init_params(1)
+    _, X, G, t = data()
+    g = mlp.grad(theta, X, G, t)
+    rng = np.random.default_rng(2)
+    idx = rng.choice(mlp.N_PARAMS, 60, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(mlp.N_PARAMS)
+        e[i] = h
+        fd = (mlp.loss(theta + e, X, G, t) - mlp.loss(theta - e, X, G, t)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(fd)) + 1e-9, (i, fd, g[i])
+
+
+def test_weights_are_convex():
+    theta = mlp.init_params(3)
+    _, X, _, _ = data()
+    w, _ = mlp.forward(theta, X)
+    assert np.all(w > 0) and np.allclose(w.sum(axis=1), 1.0, atol=1e-15)
+
+
+def test_ideal_weight_network_is_the_linear_5th_order_scheme():
+    """With W3 = 0 and b3 = log(delta) the network returns the ideal weights
+    (1/10, 6/10, 3/10) of Eq. weno5_delta: the face value is the linear
+    5th-order upwind combination (2, -13, 47, 27, -3)/60."""
+    theta = np.zeros(mlp.N_PARAMS)
+    theta[1344:1347] = np.log([0.1, 0.6, 0.3])
+    V, _, _, _ = data()
+    ref = V @ np.array([2, -13, 47, 27, -3]) / 60.0
+    np.testing.assert_allclose(mlp.face_values(theta, V), ref, rtol=1e-13, atol=1e-13)
+    for v in V[:8]:
+        assert abs(oracle.weno5_learned(theta, v) - v @ np.array([2, -13, 47, 27, -3]) / 60.0) < 1e-13
+
+
+def test_c_forward_matches_numpy():
+    theta = mlp.init_params(4)
+    V, _, _, _ = data(32, 5)
+    ref = mlp.face_values(theta, V)
+    got = np.array([oracle.weno5_learned(theta, v) for v in V])
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13)
+
+
+def test_vanishing_indicator_falls_back_to_table():
+    theta = mlp.init_params(6)
+    for v in ([2.0, 2.0, 2.0, 1.1, 0.3], [1.3, 2.0, 2.0, 2.0, 2.0], [2.0] * 5):
+        assert oracle.weno5_learned(theta, v) == oracle.weno5(v)
+
+
+def test_learned_weights_shift_and_scale_invariant():
+    theta = mlp.init_params(7)
+    V, _, _, _ = data(16, 8)
+    for v in V:
+        _, w1 = oracle.weno5_learned(theta, v, return_weights=True)
+        _, w2 = oracle.weno5_learned(theta, 4.0 * v - 1.5, return_weights=True)
+        np.testing.assert_allclose(w1, w2, rtol=1e-12)
