@@ -72,9 +72,10 @@ enum {
 /* Non-linear WENO weights. */
 enum {
     OLB_WENO_JS = 0,     /* Jiang-Shu weights of Eq. weno5_omega, Table tab:weno */
-    OLB_WENO_LEARNED = 1 /* weights from a trained network (olb_set_weno_mlp), with the
-                            Jiang-Shu weights and Table tab:weno wherever a smoothness
-                            indicator vanishes; single contexts only */
+    OLB_WENO_LEARNED = 1 /* weights from a trained network (olb_set_weno_mlp) where the
+                            stencil is not smooth (min sigma_q < 0.5 max sigma_q, no
+                            vanishing indicator); Jiang-Shu weights and Table tab:weno
+                            elsewhere; single contexts only */
 };
 
 /* Problem statement (Sec. 2, Sec. 3).  Walls: index 0 is the wall at x = 0,
@@ -174,9 +175,8 @@ int olb_profile(olb_ctx *ctx, int nsteps, double *ms, int *launches);
 
 /* Shape of the stage kernel: tx x ty nodes per CTA, kp velocities advanced
  * at once (tx*ty*kp threads).  Compiled shapes (tx, ty, kp): (8,8,4),
- * (16,8,2), (16,8,1), (32,8,1), (32,16,1) -- the last only for
- * OLB_FP32_KAHAN (its FP64 tile exceeds the shared memory of a CTA);
- * olb_create picks one from the grid size.  olb_set_tile returns
+ * (16,8,2), (16,8,1), (32,8,1), (32,16,1); olb_create picks one from the
+ * grid size.  With OLB_WENO_LEARNED only (8,8,4), (16,8,2), (32,16,1).  olb_set_tile returns
  * OLB_ERR_ARG for any other shape; results do not depend on the shape.
  * Not part of the paper (a tuning knob). */
 int olb_set_tile(olb_ctx *ctx, int tx, int ty, int kp);

@@ -13,6 +13,10 @@ Parameter vector (1347 values, the layout the library's olb_mlp_* calls
 document): W1 [32][5], b1 [32], W2 [32][32], b2 [32], W3 [3][32], b3 [3],
 row-major, concatenated.
 
+The network acts only where the stencil is not smooth in the Jiang-Shu sense
+(min sigma_q < 0.5 max sigma_q, sigma_q of Eq. weno5_sigma) and no indicator
+vanishes; elsewhere the Jiang-Shu weights apply (guard()).
+
 Training objective: the interface value v2 + sum_q w_q G_q (G_q the candidate
 values minus v2, Eq. weno5_flux) should match a target t; in normalised units
 the per-sample loss is (sum_q w_q G_q / r - (t - v2) / r)^2, r = max - min,
@@ -116,3 +120,23 @@ def face_values(theta, V):
     X, _ = normalise(V)
     w, _ = forward(theta, X)
     return np.asarray(V)[:, 2] + (w * candidates(V)).sum(axis=1)
+
+
+GUARD = 0.5
+
+
+def sigmas(V):
+    """Smoothness indicators of Eq. weno5_sigma of stencils V [S][5]."""
+    V = np.asarray(V, dtype=np.float64)
+    v0, v1, v2, v3, v4 = V.T
+    s1 = 13 / 12 * (v0 - 2 * v1 + v2) ** 2 + 0.25 * (v0 - 4 * v1 + 3 * v2) ** 2
+    s2 = 13 / 12 * (v1 - 2 * v2 + v3) ** 2 + 0.25 * (v1 - v3) ** 2
+    s3 = 13 / 12 * (v2 - 2 * v3 + v4) ** 2 + 0.25 * (3 * v2 - 4 * v3 + v4) ** 2
+    return np.stack([s1, s2, s3], axis=1)
+
+
+def network_acts(V):
+    """Rows where the network's weights are used: no vanishing indicator and
+    min sigma < GUARD max sigma."""
+    S = sigmas(V)
+    return (S.min(axis=1) > 0) & (S.min(axis=1) < GUARD * S.max(axis=1))

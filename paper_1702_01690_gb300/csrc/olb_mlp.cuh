@@ -14,6 +14,11 @@ namespace olb {
 constexpr int MLP_IN = 5, MLP_H = 32, MLP_OUT = 3;
 constexpr int MLP_W1 = 0, MLP_B1 = 160, MLP_W2 = 192, MLP_B2 = 1216, MLP_W3 = 1248, MLP_B3 = 1344;
 constexpr int MLP_P = 1347;
+// The network acts only where the stencil is not smooth in the Jiang-Shu
+// sense: min sigma_q < MLP_GUARD max sigma_q.  Where the three indicators are
+// within that factor (smooth data, for which the Jiang-Shu weights approach
+// the ideal weights and keep 5th order) the Jiang-Shu weights are used.
+constexpr double MLP_GUARD = 0.5;
 
 // Weights of one stencil; th points to the parameters (shared memory in the
 // stage kernel).  x: normalised stencil.
@@ -55,9 +60,10 @@ __device__ __forceinline__ void mlp_weights(const float *__restrict__ th, const 
 
 // Learned WENO-5 interface value (without p/m) of the upwind-ordered stencil:
 // where any smoothness indicator vanishes the Jiang-Shu weights with Table
-// tab:weno apply (constant ghost layers keep their exact flux); otherwise
-// v2 + sum_q w_q G_q with the network's weights.  The network runs in FP32;
-// the candidates are combined in the population precision.
+// tab:weno apply (constant ghost layers keep their exact flux), and so do
+// they where the stencil is smooth (min sigma_q >= MLP_GUARD max sigma_q);
+// otherwise v2 + sum_q w_q G_q with the network's weights.  The network runs
+// in FP32; the candidates are combined in the population precision.
 template <typename real>
 __device__ __forceinline__ real weno5_learned(const float *__restrict__ th, real v0, real v1, real v2, real v3,
                                               real v4)
@@ -66,9 +72,14 @@ __device__ __forceinline__ real weno5_learned(const float *__restrict__ th, real
     const real a1 = d12 - d01, b1 = fma(real(3), d12, -d01);
     const real a2 = d23 - d12, b2 = d12 + d23;
     const real a3 = d34 - d23, b3 = fma(real(-3), d23, d34);
+    const real s1 = fma(real(13) * a1, a1, real(3) * b1 * b1);
+    const real s2 = fma(real(13) * a2, a2, real(3) * b2 * b2);
+    const real s3 = fma(real(13) * a3, a3, real(3) * b3 * b3);
+    const real smin = s1 < s2 ? (s1 < s3 ? s1 : s3) : (s2 < s3 ? s2 : s3);
+    const real smax = s1 > s2 ? (s1 > s3 ? s1 : s3) : (s2 > s3 ? s2 : s3);
     const bool zero = (a1 == real(0) && b1 == real(0)) || (a2 == real(0) && b2 == real(0)) ||
                       (a3 == real(0) && b3 == real(0));
-    if (zero) return weno5(v0, v1, v2, v3, v4);
+    if (zero || smin >= real(MLP_GUARD) * smax) return weno5(v0, v1, v2, v3, v4);
     real mx = v0, mn = v0;
     mx = v1 > mx ? v1 : mx;
     mn = v1 < mn ? v1 : mn;

@@ -15,8 +15,10 @@ of Eq. weno5_omega.  Its training data come from this solver:
   differences of orders 6 and 4 on the fine line at the interface, which is a
   fine node when ratio is even.
 
-Stencils whose smoothness indicators vanish (the network is not used there:
-Table tab:weno applies) and flat stencils are dropped.  Inputs are
+Only stencils on which the network acts are kept: no vanishing smoothness
+indicator (Table tab:weno applies there) and min sigma_q < 0.5 max sigma_q
+(smooth stencils keep the Jiang-Shu weights, which approach the ideal weights
+and keep 5th order).  Inputs are
 normalised as x = (v - mean)/(max - min); the candidate offsets G_q (Eq.
 weno5_flux minus the centre value) and the target offset are divided by the
 same range.  Training runs on the GPU through olb_mlp_train.
@@ -26,6 +28,24 @@ from __future__ import annotations
 import numpy as np
 
 from . import inputs
+
+
+GUARD = 0.5
+
+
+def _sigmas(V):
+    V = np.asarray(V, dtype=np.float64)
+    d = np.diff(V, axis=1)
+    a1, b1 = d[:, 1] - d[:, 0], 3 * d[:, 1] - d[:, 0]
+    a2, b2 = d[:, 2] - d[:, 1], d[:, 1] + d[:, 2]
+    a3, b3 = d[:, 3] - d[:, 2], d[:, 3] - 3 * d[:, 2]
+    return np.stack([13 * a1 ** 2 + 3 * b1 ** 2, 13 * a2 ** 2 + 3 * b2 ** 2, 13 * a3 ** 2 + 3 * b3 ** 2], axis=1)
+
+
+def network_acts(V):
+    """Rows of stencils V on which the network's weights are used."""
+    S = _sigmas(V)
+    return (~_js_sigma_zero(V)) & (S.min(axis=1) < GUARD * S.max(axis=1))
 
 
 def _js_sigma_zero(V):
@@ -71,12 +91,12 @@ def line_samples(line, ratio: int = 4):
 
 
 def normalised_samples(V, t):
-    """x, Gn, tn (float32) for stencils V and targets t; drops stencils the
-    network never sees (vanishing indicators, zero range)."""
+    """x, Gn, tn (float32) for stencils V and targets t, keeping only the
+    stencils the network acts on."""
     V = np.asarray(V, dtype=np.float64)
     t = np.asarray(t, dtype=np.float64)
     r = V.max(axis=1) - V.min(axis=1)
-    keep = (~_js_sigma_zero(V)) & (r > 1e-13 * np.maximum(np.abs(V).max(axis=1), 1e-300))
+    keep = network_acts(V) & (r > 1e-13 * np.maximum(np.abs(V).max(axis=1), 1e-300))
     V, t, r = V[keep], t[keep], r[keep]
     x = (V - V.mean(axis=1, keepdims=True)) / r[:, None]
     Gn = candidate_offsets(V) / r[:, None]
@@ -167,7 +187,7 @@ def js_face_values(V):
 
 def learned_face_values(theta, V):
     """Interface values with the network's weights (FP64 evaluation on the
-    host, Table tab:weno where an indicator vanishes)."""
+    host; Jiang-Shu weights where the network does not act)."""
     V = np.asarray(V, dtype=np.float64)
     th = np.asarray(theta, dtype=np.float64)
     W1, b1 = th[:160].reshape(32, 5), th[160:192]
@@ -181,7 +201,7 @@ def learned_face_values(theta, V):
     w = np.exp(z)
     w /= w.sum(axis=1, keepdims=True)
     out = V[:, 2] + (w * candidate_offsets(V)).sum(axis=1)
-    zero = _js_sigma_zero(V)
-    if zero.any():
-        out[zero] = js_face_values(V[zero])
+    js = ~network_acts(V)
+    if js.any():
+        out[js] = js_face_values(V[js])
     return out

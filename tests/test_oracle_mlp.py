@@ -46,19 +46,27 @@ def test_ideal_weight_network_is_the_linear_5th_order_scheme():
     5th-order upwind combination (2, -13, 47, 27, -3)/60."""
     theta = np.zeros(mlp.N_PARAMS)
     theta[1344:1347] = np.log([0.1, 0.6, 0.3])
-    V, _, _, _ = data()
+    V, _, _, _ = data(400)
     ref = V @ np.array([2, -13, 47, 27, -3]) / 60.0
     np.testing.assert_allclose(mlp.face_values(theta, V), ref, rtol=1e-13, atol=1e-13)
-    for v in V[:8]:
-        assert abs(oracle.weno5_learned(theta, v) - v @ np.array([2, -13, 47, 27, -3]) / 60.0) < 1e-13
+    acts = mlp.network_acts(V)
+    assert acts.sum() > 20 and (~acts).sum() > 20
+    for v, a in zip(V, acts):
+        expect = v @ np.array([2, -13, 47, 27, -3]) / 60.0 if a else oracle.weno5(v)
+        assert abs(oracle.weno5_learned(theta, v) - expect) < 1e-13
 
 
 def test_c_forward_matches_numpy():
+    """The oracle's learned face value: the numpy network where it acts
+    (min sigma < 0.5 max sigma), the Jiang-Shu value elsewhere."""
     theta = mlp.init_params(4)
-    V, _, _, _ = data(32, 5)
+    V, _, _, _ = data(200, 5)
     ref = mlp.face_values(theta, V)
+    acts = mlp.network_acts(V)
     got = np.array([oracle.weno5_learned(theta, v) for v in V])
-    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13)
+    js = np.array([oracle.weno5(v) for v in V])
+    np.testing.assert_allclose(got[acts], ref[acts], rtol=1e-13, atol=1e-13)
+    np.testing.assert_array_equal(got[~acts], js[~acts])
 
 
 def test_vanishing_indicator_falls_back_to_table():

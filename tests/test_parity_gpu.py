@@ -329,10 +329,10 @@ def test_every_tile_shape_gives_identical_results(olb, side_x):
             assert np.array_equal(f, ref), shape
     with pytest.raises(olb.OlbError):
         ctx.set_tile(8, 8, 1)
-    with pytest.raises(olb.OlbError):  # FP64 32 x 16 does not fit in shared memory
-        ctx.set_tile(32, 16, 1)
-    c32 = olb.create(p, olb.FP32_KAHAN)
-    c32.set_tile(32, 16, 1)
+    ctx.set_tile(32, 16, 1)
+    ctx.init_fields(*fl)
+    ctx.step(4)
+    assert np.array_equal(ctx.get_populations(), ref)
 
 
 def test_fp32_kahan_fine_grid_laplace(olb):
