@@ -19,9 +19,12 @@ Only stencils on which the network acts are kept: no vanishing smoothness
 indicator (Table tab:weno applies there) and min sigma_q < 0.5 max sigma_q
 (smooth stencils keep the Jiang-Shu weights, which approach the ideal weights
 and keep 5th order).  Inputs are
-normalised as x = (v - mean)/(max - min); the candidate offsets G_q (Eq.
-weno5_flux minus the centre value) and the target offset are divided by the
-same range.  Training runs on the GPU through olb_mlp_train.
+normalised as x = (v - mean)/(max - min) (the network's input); the
+candidate offsets G_q (Eq. weno5_flux minus the centre value) and the target
+offset are divided by the magnitude of the population on its grid line
+(max |f| of the line), so that the loss weighs every velocity's interface
+errors relative to that velocity's size.  Training runs on the GPU through
+olb_mlp_train.
 """
 from __future__ import annotations
 
@@ -64,7 +67,8 @@ def candidate_offsets(V):
 
 
 def line_samples(line, ratio: int = 4):
-    """Stencils and targets from one periodic fine line (ratio even)."""
+    """Stencils, targets and the line's magnitude max |f| from one periodic
+    fine line (ratio even)."""
     f = np.asarray(line, dtype=np.float64)
     L = f.size
     h = float(ratio)  # in fine-node units; targets are scale-free below
@@ -87,21 +91,24 @@ def line_samples(line, ratio: int = 4):
         neg = np.stack([c[(i + k) % n] for k in (3, 2, 1, 0, -1)], axis=1)
         Vs += [pos, neg]
         Ts += [target[face], target[face]]
-    return np.concatenate(Vs), np.concatenate(Ts)
+    V, T = np.concatenate(Vs), np.concatenate(Ts)
+    return V, T, np.full(len(T), np.abs(f).max())
 
 
-def normalised_samples(V, t):
-    """x, Gn, tn (float32) for stencils V and targets t, keeping only the
-    stencils the network acts on."""
+def normalised_samples(V, t, s):
+    """x, Gn, tn (float32) for stencils V, targets t and magnitudes s,
+    keeping only the stencils the network acts on; also returns the kept
+    (V, t, s)."""
     V = np.asarray(V, dtype=np.float64)
     t = np.asarray(t, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
     r = V.max(axis=1) - V.min(axis=1)
-    keep = network_acts(V) & (r > 1e-13 * np.maximum(np.abs(V).max(axis=1), 1e-300))
-    V, t, r = V[keep], t[keep], r[keep]
+    keep = network_acts(V) & (r > 1e-13 * np.maximum(np.abs(V).max(axis=1), 1e-300)) & (s > 0)
+    V, t, r, s = V[keep], t[keep], r[keep], s[keep]
     x = (V - V.mean(axis=1, keepdims=True)) / r[:, None]
-    Gn = candidate_offsets(V) / r[:, None]
-    tn = (t - V[:, 2]) / r
-    return (x.astype(np.float32), Gn.astype(np.float32), tn.astype(np.float32)), (V, t)
+    Gn = candidate_offsets(V) / s[:, None]
+    tn = (t - V[:, 2]) / s
+    return (x.astype(np.float32), Gn.astype(np.float32), tn.astype(np.float32)), (V, t, s)
 
 
 def default_sources(scale: int = 1):
@@ -125,12 +132,13 @@ def default_sources(scale: int = 1):
 
 
 def harvest(sources=None, ratio: int = 4, row_stride: int = 16, velocities=None):
-    """Raw stencils V [S][5] and targets t [S] from solver runs (FP64 path)."""
+    """Raw stencils V [S][5], targets t [S] and line magnitudes s [S] from
+    solver runs (FP64 path)."""
     from . import olb
     if sources is None:
         sources = default_sources()
     moving = velocities if velocities is not None else [k for k in range(25) if k // 5 != 2]
-    Vs, Ts = [], []
+    Vs, Ts, Ss = [], [], []
     for p, fields, steps in sources:
         ctx = olb.create(p)
         ctx.init_fields(*fields)
@@ -139,10 +147,11 @@ def harvest(sources=None, ratio: int = 4, row_stride: int = 16, velocities=None)
         ctx.close()
         for k in moving:
             for j in range(0, p.ny, row_stride):  # x lines (periodic runs only)
-                V, t = line_samples(f[k, j, :], ratio)
+                V, t, s = line_samples(f[k, j, :], ratio)
                 Vs.append(V)
                 Ts.append(t)
-    return np.concatenate(Vs), np.concatenate(Ts)
+                Ss.append(s)
+    return np.concatenate(Vs), np.concatenate(Ts), np.concatenate(Ss)
 
 
 def train(x, Gn, tn, epochs: int = 40, batch: int = 4096, lr: float = 2e-3, seed: int = 0):
