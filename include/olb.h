@@ -73,7 +73,7 @@ enum {
 enum {
     OLB_WENO_JS = 0,     /* Jiang-Shu weights of Eq. weno5_omega, Table tab:weno */
     OLB_WENO_LEARNED = 1 /* weights from a trained network (olb_set_weno_mlp) where the
-                            stencil is not smooth (min sigma_q < 0.5 max sigma_q, no
+                            stencil is not smooth (min sigma_q < 0.9 max sigma_q, no
                             vanishing indicator); Jiang-Shu weights and Table tab:weno
                             elsewhere; single contexts only */
 };

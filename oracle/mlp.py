@@ -14,7 +14,7 @@ document): W1 [32][5], b1 [32], W2 [32][32], b2 [32], W3 [3][32], b3 [3],
 row-major, concatenated.
 
 The network acts only where the stencil is not smooth in the Jiang-Shu sense
-(min sigma_q < 0.5 max sigma_q, sigma_q of Eq. weno5_sigma) and no indicator
+(min sigma_q < 0.9 max sigma_q, sigma_q of Eq. weno5_sigma) and no indicator
 vanishes; elsewhere the Jiang-Shu weights apply (guard()).
 
 Training objective: the interface value v2 + sum_q w_q G_q (G_q the candidate
@@ -122,7 +122,7 @@ def face_values(theta, V):
     return np.asarray(V)[:, 2] + (w * candidates(V)).sum(axis=1)
 
 
-GUARD = 0.5
+GUARD = 0.9
 
 
 def sigmas(V):

@@ -301,7 +301,7 @@ double orc_weno5(const double *v, double *wout)
  * (tanh, tanh, softmax) from the normalised stencil (v - mean)/(max - min).
  * Where any indicator vanishes, Table tab:weno applies as in orc_weno5, so
  * constant ghost layers keep their exact fluxes; where the stencil is smooth
- * (min sigma >= 0.5 max sigma) the Jiang-Shu weights apply.  theta: 1347
+ * (min sigma >= 0.9 max sigma) the Jiang-Shu weights apply.  theta: 1347
  * parameters, W1 [32][5], b1 [32], W2 [32][32], b2 [32], W3 [3][32], b3 [3]. */
 #define MLP_H 32
 double orc_weno5_learned(const double *theta, const double *v, double *wout)
@@ -319,7 +319,7 @@ double orc_weno5_learned(const double *theta, const double *v, double *wout)
         if (sg[q] < smin) smin = sg[q];
         if (sg[q] > smax) smax = sg[q];
     }
-    if (smin >= 0.5 * smax) return orc_weno5(v, wout);
+    if (smin >= 0.9 * smax) return orc_weno5(v, wout);
     const double *W1 = theta, *b1 = theta + 160, *W2 = theta + 192, *b2 = theta + 1216;
     const double *W3 = theta + 1248, *b3 = theta + 1344;
     double mean = 0.0, mx = v[0], mn = v[0];

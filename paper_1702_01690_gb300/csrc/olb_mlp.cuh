@@ -18,7 +18,7 @@ constexpr int MLP_P = 1347;
 // sense: min sigma_q < MLP_GUARD max sigma_q.  Where the three indicators are
 // within that factor (smooth data, for which the Jiang-Shu weights approach
 // the ideal weights and keep 5th order) the Jiang-Shu weights are used.
-constexpr double MLP_GUARD = 0.5;
+constexpr double MLP_GUARD = 0.9;
 
 // Weights of one stencil; th points to the parameters (shared memory in the
 // stage kernel).  x: normalised stencil.

@@ -86,21 +86,22 @@ def node_y(ny: int, ds: float) -> np.ndarray:
     return (np.arange(ny) + 0.5) * ds
 
 
-def shear_wave(nx: int, ny: int, ds: float, n0=1.0, T0=1.1, u0=1e-3, V=0.0):
-    """Uniform n, T; u_y = u0 sin(2 pi x); u_x = V."""
+def shear_wave(nx: int, ny: int, ds: float, n0=1.0, T0=1.1, u0=1e-3, V=0.0, m: int = 1):
+    """Uniform n, T; u_y = u0 sin(2 pi m x); u_x = V."""
     x = node_x(nx, ds)
     n = np.full((ny, nx), float(n0))
     T = np.full((ny, nx), float(T0))
     ux = np.full((ny, nx), float(V))
-    uy = np.tile(u0 * np.sin(2.0 * math.pi * x), (ny, 1))
+    uy = np.tile(u0 * np.sin(2.0 * math.pi * m * x), (ny, 1))
     return n, ux, uy, T
 
 
-def longitudinal_wave(nx: int, ny: int, ds: float, n0=1.0, T0=1.1, u0=1e-3):
+def longitudinal_wave(nx: int, ny: int, ds: float, n0=1.0, T0=1.1, u0=1e-3, m: int = 1):
+    """Uniform n, T; u_x = u0 sin(2 pi m x); u_y = 0."""
     x = node_x(nx, ds)
     n = np.full((ny, nx), float(n0))
     T = np.full((ny, nx), float(T0))
-    ux = np.tile(u0 * np.sin(2.0 * math.pi * x), (ny, 1))
+    ux = np.tile(u0 * np.sin(2.0 * math.pi * m * x), (ny, 1))
     uy = np.zeros((ny, nx))
     return n, ux, uy, T
 

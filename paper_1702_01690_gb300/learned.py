@@ -16,14 +16,13 @@ of Eq. weno5_omega.  Its training data come from this solver:
   fine node when ratio is even.
 
 Only stencils on which the network acts are kept: no vanishing smoothness
-indicator (Table tab:weno applies there) and min sigma_q < 0.5 max sigma_q
-(smooth stencils keep the Jiang-Shu weights, which approach the ideal weights
-and keep 5th order).  Inputs are
+indicator (Table tab:weno applies there) and min sigma_q < 0.9 max sigma_q
+(on smooth data sigma_min / sigma_max = 1 - O(h), so as the grid is refined
+every smooth stencil passes to the Jiang-Shu weights, which approach the
+ideal weights and keep 5th order).  Inputs are
 normalised as x = (v - mean)/(max - min) (the network's input); the
 candidate offsets G_q (Eq. weno5_flux minus the centre value) and the target
-offset are divided by the magnitude of the population on its grid line
-(max |f| of the line), so that the loss weighs every velocity's interface
-errors relative to that velocity's size.  Training runs on the GPU through
+offset are divided by the same range.  Training runs on the GPU through
 olb_mlp_train.
 """
 from __future__ import annotations
@@ -33,7 +32,7 @@ import numpy as np
 from . import inputs
 
 
-GUARD = 0.5
+GUARD = 0.9
 
 
 def _sigmas(V):
@@ -96,9 +95,9 @@ def line_samples(line, ratio: int = 4):
 
 
 def normalised_samples(V, t, s):
-    """x, Gn, tn (float32) for stencils V, targets t and magnitudes s,
-    keeping only the stencils the network acts on; also returns the kept
-    (V, t, s)."""
+    """x, Gn, tn (float32) for stencils V and targets t, keeping only the
+    stencils the network acts on; also returns the kept (V, t, r), r the
+    stencil ranges (s, the line magnitudes, only filters empty lines)."""
     V = np.asarray(V, dtype=np.float64)
     t = np.asarray(t, dtype=np.float64)
     s = np.asarray(s, dtype=np.float64)
@@ -106,9 +105,9 @@ def normalised_samples(V, t, s):
     keep = network_acts(V) & (r > 1e-13 * np.maximum(np.abs(V).max(axis=1), 1e-300)) & (s > 0)
     V, t, r, s = V[keep], t[keep], r[keep], s[keep]
     x = (V - V.mean(axis=1, keepdims=True)) / r[:, None]
-    Gn = candidate_offsets(V) / s[:, None]
-    tn = (t - V[:, 2]) / s
-    return (x.astype(np.float32), Gn.astype(np.float32), tn.astype(np.float32)), (V, t, s)
+    Gn = candidate_offsets(V) / r[:, None]
+    tn = (t - V[:, 2]) / r
+    return (x.astype(np.float32), Gn.astype(np.float32), tn.astype(np.float32)), (V, t, r)
 
 
 def default_sources(scale: int = 1):
@@ -119,10 +118,15 @@ def default_sources(scale: int = 1):
         p, f = inputs.laplace(n, R=R, steps=4)
         out.append((p, f, 4))
     ds = 1.0 / (256 * scale)
+    p = inputs.RunParams(nx=256 * scale, ny=256 * scale, ds=ds, dt=inputs.stable_dt(ds), tau=0.01)
     for amp in (0.05, 0.2):
-        p = inputs.RunParams(nx=256 * scale, ny=256 * scale, ds=ds, dt=inputs.stable_dt(ds), tau=0.01)
         out.append((p, inputs.shear_wave(p.nx, p.ny, ds, 1.0, 0.9, amp), 4))
         out.append((p, inputs.longitudinal_wave(p.nx, p.ny, ds, 1.0, 0.9, amp), 4))
+    # waves resolved by 16 and 32 coarse nodes per wavelength (the coarse,
+    # smooth regime of the 64 x 4 shear-decay run and coarser grids)
+    for m in (2 * scale, 4 * scale):
+        out.append((p, inputs.shear_wave(p.nx, p.ny, ds, 1.0, 0.8, 0.01, m=m), 4))
+        out.append((p, inputs.longitudinal_wave(p.nx, p.ny, ds, 1.0, 1.1, 0.01, m=m), 4))
     ds = 1.0 / (512 * scale)
     p = inputs.RunParams(nx=512 * scale, ny=64, ds=ds, dt=inputs.stable_dt(ds, n_max=1.1), tau=0.005)
     n0 = 1.0 + 0.05 * inputs.band_limited_noise(p.nx, p.ny, inputs.SEED_BASE + 7, 8)
