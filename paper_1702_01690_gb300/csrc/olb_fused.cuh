@@ -60,9 +60,11 @@ struct FusedSmem {
     real ux[TY][TX];
     real uy[TY][TX];
     real T[TY][TX];
-    // F_x, F_y, n, g_k(u_x, T), g_k(u_y, T) per tile node, shared by the KP
-    // velocity lanes (with one lane they stay in registers)
-    real loc[KP > 1 ? 3 + 2 * NQ : 1][KP > 1 ? NN : 1];
+    // per tile node, shared by the KP velocity lanes (with one lane they stay
+    // in registers): the stencil sums of grad(Delta p) and grad(Laplacian n),
+    // n, inv_ds / n, g_k(u_x, T) and g_k(u_y, T)
+    static constexpr int L_DDX = 0, L_DDY = 1, L_LDX = 2, L_LDY = 3, L_N = 4, L_DN = 5, L_GX = 6, L_GY = 6 + NQ;
+    real loc[KP > 1 ? 6 + 2 * NQ : 1][KP > 1 ? NN : 1];
     real fx[KP][TY][TX + 1];
     real fy[KP][TY + 1][TX];
     real nw[2][TY];
@@ -275,11 +277,12 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     }
     __syncthreads();
 
-    // ---- 4. force and equilibrium factors at the tile nodes (lane 0)
-    real Fx = 0, Fy = 0, nn = 1, gx[NQ], gy[NQ];
-    if (active && lane_k == 0) {
-        real ddx = 0, ddy = 0, ldx = 0, ldy = 0;
-        constexpr int cy = 3, cx = 4;
+    // ---- 4. force and equilibrium factors at the tile nodes.  The four
+    // stencil sums and the two factor sets are split over the velocity lanes
+    // (KP = 4: ddx | ddy | ldx, g(u_x) | ldy, g(u_y); KP = 2: x | y parts).
+    constexpr int cy = 3, cx = 4;
+    auto grad_sum = [&](bool along_x) {
+        real acc = 0;
 #pragma unroll
         for (int l = 1; l <= 3; ++l)
 #pragma unroll
@@ -287,31 +290,74 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 const int am = m < 0 ? -m : m;
                 if (grad_w(l, am) != 0.0) {
                     const real w = real(l * grad_w(l, am));
-                    ddx = fma(w, field_diff(sm.dp[ty + cy + m][tx + cx + l], sm.dp[ty + cy + m][tx + cx - l]), ddx);
-                    ddy = fma(w, field_diff(sm.dp[ty + cy + l][tx + cx + m], sm.dp[ty + cy - l][tx + cx + m]), ddy);
+                    acc = along_x ? fma(w, field_diff(sm.dp[ty + cy + m][tx + cx + l], sm.dp[ty + cy + m][tx + cx - l]), acc)
+                                  : fma(w, field_diff(sm.dp[ty + cy + l][tx + cx + m], sm.dp[ty + cy - l][tx + cx + m]), acc);
                 }
+            }
+        return acc;
+    };
+    auto glap_sum = [&](bool along_x) {
+        real acc = 0;
+#pragma unroll
+        for (int l = 1; l <= 3; ++l)
+#pragma unroll
+            for (int m = -3; m <= 3; ++m) {
+                const int am = m < 0 ? -m : m;
                 if (glap_c(am, l) != 0.0) {
                     const real w = real(glap_c(am, l));
-                    ldx = fma(w, field_diff(sm.n[ty + cy + m][tx + cx + l], sm.n[ty + cy + m][tx + cx - l]), ldx);
-                    ldy = fma(w, field_diff(sm.n[ty + cy + l][tx + cx + m], sm.n[ty + cy - l][tx + cx + m]), ldy);
+                    acc = along_x ? fma(w, field_diff(sm.n[ty + cy + m][tx + cx + l], sm.n[ty + cy + m][tx + cx - l]), acc)
+                                  : fma(w, field_diff(sm.n[ty + cy + l][tx + cx + m], sm.n[ty + cy - l][tx + cx + m]), acc);
                 }
             }
-        nn = field_val(sm.n[ty + cy][tx + cx]);
-        const real dn = real(g.inv_ds) / nn;
-        const real sg3 = real(g.sigma) * real(g.inv_ds3);
-        Fx = fma(ddx, dn, sg3 * ldx);
-        Fy = fma(ddy, dn, sg3 * ldy);
-        eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], gx);
-        eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gy);
-        if constexpr (KP > 1) {
-            sm.loc[0][node] = Fx;
-            sm.loc[1][node] = Fy;
-            sm.loc[2][node] = nn;
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                sm.loc[3 + q][node] = gx[q];
-                sm.loc[3 + NQ + q][node] = gy[q];
+        return acc;
+    };
+    const real sg3 = real(g.sigma) * real(g.inv_ds3);
+    real Fx = 0, Fy = 0, nn = 1, gx[NQ], gy[NQ];
+    if constexpr (KP == 1) {
+        if (active) {
+            const real ddx = grad_sum(true), ddy = grad_sum(false);
+            const real ldx = glap_sum(true), ldy = glap_sum(false);
+            nn = field_val(sm.n[ty + cy][tx + cx]);
+            const real dn = real(g.inv_ds) / nn;
+            Fx = fma(ddx, dn, sg3 * ldx);
+            Fy = fma(ddy, dn, sg3 * ldy);
+            eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], gx);
+            eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gy);
+        }
+    } else {
+        static_assert(KP == 2 || KP == 4, "velocity lanes: 1, 2 or 4");
+        using Sm = FusedSmem<real, TX, TY, KP>;
+        if (active) {
+            // KP = 4: lane 0 ddx, lane 1 ddy, lane 2 ldx + g(u_x), lane 3 ldy + g(u_y)
+            // KP = 2: lane 0 the x parts, lane 1 the y parts
+            const bool lane_x = KP == 2 ? lane_k == 0 : lane_k == 2;
+            const bool lane_y = KP == 2 ? lane_k == 1 : lane_k == 3;
+            if (lane_k == 0) {
+                sm.loc[Sm::L_DDX][node] = grad_sum(true);
+                nn = field_val(sm.n[ty + cy][tx + cx]);
+                sm.loc[Sm::L_N][node] = nn;
+                sm.loc[Sm::L_DN][node] = real(g.inv_ds) / nn;
             }
+            if (lane_k == 1) sm.loc[Sm::L_DDY][node] = grad_sum(false);
+            if (lane_x) {
+                sm.loc[Sm::L_LDX][node] = glap_sum(true);
+                eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], gx);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) sm.loc[Sm::L_GX + q][node] = gx[q];
+            }
+            if (lane_y) {
+                sm.loc[Sm::L_LDY][node] = glap_sum(false);
+                eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gy);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) sm.loc[Sm::L_GY + q][node] = gy[q];
+            }
+        }
+        __syncthreads();
+        if (active) {
+            const real dn = sm.loc[Sm::L_DN][node];
+            nn = sm.loc[Sm::L_N][node];
+            Fx = fma(sm.loc[Sm::L_DDX][node], dn, sg3 * sm.loc[Sm::L_LDX][node]);
+            Fy = fma(sm.loc[Sm::L_DDY][node], dn, sg3 * sm.loc[Sm::L_LDY][node]);
         }
     }
 
@@ -321,16 +367,30 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     const real itau = real(g.inv_tau);
     const real cadv = cc * real(g.inv_ds);
     for (int kb = 0; kb < NK; kb += KP) {
-        __syncthreads();  // loc ready / the previous velocities' faces are consumed
-        // faces of the KP velocities kb .. kb+KP-1: x faces of the tile rows,
-        // then y faces of the tile columns, each computed once
-        for (int e = tid; e < KP * (nfx + nfy); e += NT) {
-            const int sub = e / (nfx + nfy), f = e - sub * (nfx + nfy);
+        // faces of the KP velocities kb .. kb+KP-1, each computed once and
+        // enumerated densely: x faces of the tile rows unless xi_x = 0 (k1 = 2),
+        // then y faces of the tile columns unless xi_y = 0 (k2 = 2)
+        int end[KP], total = 0;
+#pragma unroll
+        for (int sub = 0; sub < KP; ++sub) {
             const int k = kb + sub;
-            if (k >= NK) continue;
+            if (k < NK) total += (k / NQ != 2 ? nfx : 0) + (k % NQ != 2 ? nfy : 0);
+            end[sub] = total;
+        }
+        __syncthreads();  // the previous velocities' faces are consumed
+        for (int e = tid; e < total; e += NT) {
+            int sub = 0, start = 0;
+#pragma unroll
+            for (int q = 0; q + 1 < KP; ++q)
+                if (e >= end[q]) {
+                    sub = q + 1;
+                    start = end[q];
+                }
+            const int k = kb + sub;
             const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
+            int f = e - start;
+            if (k1 == 2) f += nfx;
             if (f < nfx) {
-                if (k1 == 2) continue;
                 const int r = f / (TX + 1), c = f - r * (TX + 1);
                 if (y0 + r < g.ny && x0 + c <= g.nx) {
                     // face at x = x0 + c: nodes x0+c-3 .. x0+c+2 are columns c+1 .. c+6
@@ -340,7 +400,6 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                                  : face_value<real, LEARNED>(mlp, row[c + 6], row[c + 5], row[c + 4], row[c + 3], row[c + 2]);
                 }
             } else {
-                if (k2 == 2) continue;
                 const int e2 = f - nfx;
                 const int r = e2 / TX, c = e2 - r * TX;
                 if (x0 + c < g.nx && y0 + r <= g.ny) {
@@ -368,9 +427,10 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             const real f = sm.pop[k][r][c];
             real feq, fxv, fyv;
             if constexpr (KP > 1) {
-                feq = sm.loc[2][node] * sm.loc[3 + k1][node] * sm.loc[3 + NQ + k2][node];
-                fxv = sm.loc[0][node];
-                fyv = sm.loc[1][node];
+                using Sm = FusedSmem<real, TX, TY, KP>;
+                feq = nn * sm.loc[Sm::L_GX + k1][node] * sm.loc[Sm::L_GY + k2][node];
+                fxv = Fx;
+                fyv = Fy;
             } else {
                 feq = nn * sel5(gx, k1) * sel5(gy, k2);
                 fxv = Fx;

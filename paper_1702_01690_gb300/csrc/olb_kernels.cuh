@@ -57,37 +57,39 @@ __device__ __forceinline__ double recip_nr(double d)
 // v0..v4 = f_{i-2} .. f_{i+2} in the upwind orientation; returns the WENO-5
 // interface value sum_q wbar_q Fhat^q (without p/m).
 //
-// In terms of the first differences d01 = v1 - v0, ..., d34 = v4 - v3:
-//   sigma_q = 13/12 a_q^2 + 1/4 b_q^2 with a_1 = d12 - d01, b_1 = 3 d12 - d01,
-//   a_2 = d23 - d12, b_2 = d12 + d23, a_3 = d34 - d23, b_3 = d34 - 3 d23
-//   (Eq. weno5_sigma), and Fhat^q = v2 + G_q with G_1 = (5 d12 - 2 d01)/6,
-//   G_2 = (d12 + 2 d23)/6, G_3 = (4 d23 - d34)/6 (the candidates of
-//   Eq. weno5_flux).  The weights only depend on ratios of the sigma_q, so
-//   12 sigma_q = 13 a_q^2 + 3 b_q^2 is used.
+// In terms of the first differences d01 = v1 - v0, ..., d34 = v4 - v3, the
+// indicators of Eq. weno5_sigma (13/12 a_q^2 + 1/4 b_q^2, a_q and b_q linear
+// in two neighbouring differences) are positive-definite quadratic forms:
+//   12 sigma_1 / 16 = d01^2 - 11/4 d01 d12 + 5/2 d12^2
+//   12 sigma_2 / 16 = d12^2 + d23^2 - 5/4 d12 d23
+//   12 sigma_3 / 16 = d34^2 - 11/4 d23 d34 + 5/2 d23^2
+// (the weights only depend on ratios of the sigma_q, so the common factor
+// 12/16 is dropped), and 6 (Fhat^q - v2) of Eq. weno5_flux are
+//   6 G_1 = 5 d12 - 2 d01,  6 G_2 = d12 + 2 d23,  6 G_3 = 4 d23 - d34.
+// A form vanishes exactly when both of its differences do (the case of
+// Table tab:weno).
 //
 // Weights: wbar_q is proportional to delta_q / sigma_q^2.  Multiplying every
-// term by (sigma_1 sigma_2 sigma_3)^2 gives weights proportional to
-// A_q = delta_q (prod_{r != q} sigma_r)^2, which needs one reciprocal, equals
-// the table row for a single vanishing indicator, and is 0/0 only when two
-// or three vanish; those cases take Table tab:weno (the ideal weights of the
-// vanishing set).  If the products underflow without an exact zero the
+// term by 10 (sigma_1 sigma_2 sigma_3)^2 gives weights proportional to
+// A_q = 10 delta_q (prod_{r != q} sigma_r)^2, which needs one reciprocal,
+// equals the table row for a single vanishing indicator, and is 0/0 only when
+// two or three vanish; those cases take Table tab:weno (the ideal weights of
+// the vanishing set).  If the products underflow without an exact zero the
 // min-scaled form delta_q (s/sigma_q)^2 is used instead.
 __device__ __forceinline__ double weno5(double v0, double v1, double v2, double v3, double v4)
 {
     const double d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
-    const double a1 = d12 - d01, b1 = fma(3.0, d12, -d01);
-    const double a2 = d23 - d12, b2 = d12 + d23;
-    const double a3 = d34 - d23, b3 = fma(-3.0, d23, d34);
-    const double s1 = fma(13.0 * a1, a1, 3.0 * b1 * b1);
-    const double s2 = fma(13.0 * a2, a2, 3.0 * b2 * b2);
-    const double s3 = fma(13.0 * a3, a3, 3.0 * b3 * b3);
-    const double G1 = fma(5.0 / 6.0, d12, (-1.0 / 3.0) * d01);
-    const double G2 = fma(1.0 / 3.0, d23, (1.0 / 6.0) * d12);
-    const double G3 = fma(2.0 / 3.0, d23, (-1.0 / 6.0) * d34);
+    const double q12 = d12 * d12, q23 = d23 * d23;
+    const double s1 = fma(d01, fma(-2.75, d12, d01), 2.5 * q12);
+    const double s2 = fma(-1.25 * d12, d23, q12 + q23);
+    const double s3 = fma(d34, fma(-2.75, d23, d34), 2.5 * q23);
+    const double G1 = fma(5.0, d12, -2.0 * d01);
+    const double G2 = fma(2.0, d23, d12);
+    const double G3 = fma(4.0, d23, -d34);
     const double p1 = s2 * s3, p2 = s1 * s3, p3 = s1 * s2;
-    const double A1 = (0.1 * p1) * p1, A2 = (0.6 * p2) * p2, A3 = (0.3 * p3) * p3;
+    const double A1 = p1 * p1, A2 = (6.0 * p2) * p2, A3 = (3.0 * p3) * p3;
     const double den = A1 + A2 + A3;
-    if (den > 2.3e-308) return fma(fma(A1, G1, fma(A2, G2, A3 * G3)), recip_nr(den), v2);
+    if (den > 2.3e-308) return fma(fma(A1, G1, fma(A2, G2, A3 * G3)), recip_nr(6.0 * den), v2);
     double w1, w2, w3;
     if (s1 == 0.0 || s2 == 0.0 || s3 == 0.0) {
         w1 = (s1 == 0.0) ? 0.1 : 0.0;
@@ -100,38 +102,36 @@ __device__ __forceinline__ double weno5(double v0, double v1, double v2, double 
         w2 = 0.6 * r2 * r2;
         w3 = 0.3 * r3 * r3;
     }
-    return v2 + (w1 * G1 + w2 * G2 + w3 * G3) / (w1 + w2 + w3);
+    return v2 + (w1 * G1 + w2 * G2 + w3 * G3) / (6.0 * (w1 + w2 + w3));
 }
 
-// FP32 form (same differences): the products of four squared indicators
-// underflow in single precision, so the weights are always the min-scaled
-// delta_q (s/sigma_q)^2 (same normalised weights), with Table tab:weno when
-// an indicator vanishes.
+// FP32 form (same forms and candidates): the products of four squared
+// indicators underflow in single precision, so the weights are always the
+// min-scaled 10 delta_q (s/sigma_q)^2 (same normalised weights), with Table
+// tab:weno when an indicator vanishes.
 __device__ __forceinline__ float weno5(float v0, float v1, float v2, float v3, float v4)
 {
     const float d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
-    const float a1 = d12 - d01, b1 = fmaf(3.0f, d12, -d01);
-    const float a2 = d23 - d12, b2 = d12 + d23;
-    const float a3 = d34 - d23, b3 = fmaf(-3.0f, d23, d34);
-    const float s1 = fmaf(13.0f * a1, a1, 3.0f * b1 * b1);
-    const float s2 = fmaf(13.0f * a2, a2, 3.0f * b2 * b2);
-    const float s3 = fmaf(13.0f * a3, a3, 3.0f * b3 * b3);
-    const float G1 = fmaf(5.0f / 6.0f, d12, (-1.0f / 3.0f) * d01);
-    const float G2 = fmaf(1.0f / 3.0f, d23, (1.0f / 6.0f) * d12);
-    const float G3 = fmaf(2.0f / 3.0f, d23, (-1.0f / 6.0f) * d34);
+    const float q12 = d12 * d12, q23 = d23 * d23;
+    const float s1 = fmaf(d01, fmaf(-2.75f, d12, d01), 2.5f * q12);
+    const float s2 = fmaf(-1.25f * d12, d23, q12 + q23);
+    const float s3 = fmaf(d34, fmaf(-2.75f, d23, d34), 2.5f * q23);
+    const float G1 = fmaf(5.0f, d12, -2.0f * d01);
+    const float G2 = fmaf(2.0f, d23, d12);
+    const float G3 = fmaf(4.0f, d23, -d34);
     float w1, w2, w3;
     const float s = fminf(s1, fminf(s2, s3));
     if (s > 0.0f) {
         const float r1 = __fdividef(s, s1), r2 = __fdividef(s, s2), r3 = __fdividef(s, s3);
-        w1 = 0.1f * r1 * r1;
-        w2 = 0.6f * r2 * r2;
-        w3 = 0.3f * r3 * r3;
+        w1 = r1 * r1;
+        w2 = (6.0f * r2) * r2;
+        w3 = (3.0f * r3) * r3;
     } else {
-        w1 = (s1 == 0.0f) ? 0.1f : 0.0f;
-        w2 = (s2 == 0.0f) ? 0.6f : 0.0f;
-        w3 = (s3 == 0.0f) ? 0.3f : 0.0f;
+        w1 = (s1 == 0.0f) ? 1.0f : 0.0f;
+        w2 = (s2 == 0.0f) ? 6.0f : 0.0f;
+        w3 = (s3 == 0.0f) ? 3.0f : 0.0f;
     }
-    return fmaf(fmaf(w1, G1, fmaf(w2, G2, w3 * G3)), __fdividef(1.0f, w1 + w2 + w3), v2);
+    return fmaf(fmaf(w1, G1, fmaf(w2, G2, w3 * G3)), __fdividef(1.0f, 6.0f * (w1 + w2 + w3)), v2);
 }
 
 // ---------------------------------------------------------------- helpers
