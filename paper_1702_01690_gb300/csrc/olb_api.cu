@@ -285,14 +285,28 @@ static cudaError_t prepare_tile(olb_ctx *c)
 
 // Default shape: 16 x 8 nodes with 2 velocity lanes (FP64) or 32 x 16
 // nodes (FP32) when that still gives every SM two CTAs; otherwise 8 x 8
-// nodes with 4 velocity lanes, so that small grids (e.g. 1024 x 8) still
-// put 8 warps on each busy SM.  olb_set_tile / olb_autotune override.
+// nodes with 4 (FP64, learned weights) or 8 (FP32) velocity lanes, so that
+// small grids (e.g. 1024 x 8) still put 8-16 warps on each busy SM (the
+// fastest shapes measured on a GB300).  Small grids take 7 x 8 tiles with 8
+// lanes instead when that lowers the most nodes any SM has to advance
+// (1024 x 8: 147 tiles of 56 nodes rather than 128 of 64 on 152 SMs).
+// olb_set_tile overrides.
 static void default_tile(olb_ctx *c)
 {
-    const int big = is_fp64(c) ? 1 : 4;  // index into TILE_*
-    const long long ctas = (long long)((c->geo.nx + TILE_X[big] - 1) / TILE_X[big]) *
-                           ((c->geo.ny + TILE_Y[big] - 1) / TILE_Y[big]);
-    const int k = ctas >= 2 * 152 ? big : 0;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    const bool learned = c->p.weno_mode == OLB_WENO_LEARNED;
+    const int big = is_fp64(c) ? 1 : 4;  // indices into TILE_*
+    const int small = is_fp64(c) || learned ? 0 : 5;
+    const int narrow = 6;
+    auto tiles = [&](int k) {
+        return (long long)((c->geo.nx + TILE_X[k] - 1) / TILE_X[k]) * ((c->geo.ny + TILE_Y[k] - 1) / TILE_Y[k]);
+    };
+    auto most_nodes = [&](int k) { return (tiles(k) + sms - 1) / sms * TILE_X[k] * TILE_Y[k]; };
+    int k = small;
+    if (tiles(big) >= 2 * sms) k = big;
+    else if (!learned && most_nodes(narrow) < most_nodes(small)) k = narrow;
     c->tx = TILE_X[k];
     c->ty = TILE_Y[k];
     c->kp = TILE_K[k];

@@ -14,7 +14,8 @@
 //      for the incoming velocities;
 //   4. force F = grad(Delta p)/n + sigma grad(Laplacian n) at the tile nodes
 //      from the 49-point stencils (Eqs. F_def, stencil_grad, stencil_glap);
-//   5. for KP velocities at a time (one group of TX*TY threads each): every x
+//   5. for KP velocities at a time (one lane of TX*TY threads, rounded up to
+//      whole warps, each): every x
 //      and y face of the tile once (WENO-5, Eqs. weno5_*), then per node the
 //      flux differences, the momentum derivative (Eq. derf), BGK with f^eq
 //      (Eqs. feq, g_alpha) and the RK-3 combination of Eq. rk3, written to
@@ -52,7 +53,9 @@ __device__ __forceinline__ float field_val(float2 a) { return a.x + a.y; }
 
 template <typename real, int TX, int TY, int KP>
 struct FusedSmem {
-    static constexpr int HX = TX + 8, HY = TY + 6, NN = TX * TY, NT = NN * KP;
+    // LS: threads per velocity lane, the tile's nodes rounded up to whole
+    // warps (so that every lane starts on a warp); NT threads in all
+    static constexpr int HX = TX + 8, HY = TY + 6, NN = TX * TY, LS = (NN + 31) / 32 * 32, NT = LS * KP;
     using fld = typename FieldT<real>::type;
     real pop[NK][HY][HX];
     fld n[HY][HX];
@@ -62,9 +65,9 @@ struct FusedSmem {
     real T[TY][TX];
     // per tile node, shared by the KP velocity lanes (with one lane they stay
     // in registers): the stencil sums of grad(Delta p) and grad(Laplacian n),
-    // n, inv_ds / n, g_k(u_x, T) and g_k(u_y, T)
-    static constexpr int L_DDX = 0, L_DDY = 1, L_LDX = 2, L_LDY = 3, L_N = 4, L_DN = 5, L_GX = 6, L_GY = 6 + NQ;
-    real loc[KP > 1 ? 6 + 2 * NQ : 1][KP > 1 ? NN : 1];
+    // inv_ds / n, E_q = (c/tau) n g_q(u_x, T) and g_q(u_y, T)
+    static constexpr int L_DDX = 0, L_DDY = 1, L_LDX = 2, L_LDY = 3, L_DN = 4, L_E = 5, L_GY = 5 + NQ;
+    real loc[KP > 1 ? 5 + 2 * NQ : 1][KP > 1 ? NN : 1];
     real fx[KP][TY][TX + 1];
     real fy[KP][TY + 1][TX];
     real nw[2][TY];
@@ -107,10 +110,10 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
 
     // thread = (tile node, velocity lane): KP velocities are advanced at once
     const int tid = threadIdx.x;
-    const int node = tid % NN, lane_k = tid / NN;
+    const int node = tid % S::LS, lane_k = tid / S::LS;
     const int tx = node % TX, ty = node / TX;
     const int i = x0 + tx, j = y0 + ty;
-    const bool active = (i < g.nx) && (j < g.ny);
+    const bool active = (node < NN) && (i < g.nx) && (j < g.ny);
 
     // ---- 1. populations of the region (c <-> x = x0 - 4 + c, r <-> y = y0 - 3 + r)
     for (int e = tid; e < HY * HX; e += NT) {
@@ -130,9 +133,10 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     }
     __syncthreads();
 
-    // ---- 2. moments at every fluid position of the region
-    for (int e = tid; e < HY * HX; e += NT) {
-        const int r = e / HX, c = e - r * HX;
+    // ---- 2. moments at every fluid position of the region that the 7 x 7
+    // force stencils reach (columns 1 .. HX-2)
+    for (int e = tid; e < HY * (HX - 2); e += NT) {
+        const int r = e / (HX - 2), c = e - r * (HX - 2) + 1;
         const int gx = x0 - 4 + c;
         if (g.walls && (gx < 0 || gx >= g.nx)) continue;
         double n, jx, jy, en;
@@ -311,42 +315,50 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             }
         return acc;
     };
+    // With c the stage's coefficient of dt L (Eq. rk3), the node update below
+    // needs per node G = c F, E_q = (c/tau) n g_q(u_x, T) and g_q(u_y, T).
     const real sg3 = real(g.sigma) * real(g.inv_ds3);
-    real Fx = 0, Fy = 0, nn = 1, gx[NQ], gy[NQ];
+    const real cit = cc * real(g.inv_tau);
+    real Gx = 0, Gy = 0, E[NQ], gy[NQ];
     if constexpr (KP == 1) {
         if (active) {
             const real ddx = grad_sum(true), ddy = grad_sum(false);
             const real ldx = glap_sum(true), ldy = glap_sum(false);
-            nn = field_val(sm.n[ty + cy][tx + cx]);
+            const real nn = field_val(sm.n[ty + cy][tx + cx]);
             const real dn = real(g.inv_ds) / nn;
-            Fx = fma(ddx, dn, sg3 * ldx);
-            Fy = fma(ddy, dn, sg3 * ldy);
-            eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], gx);
+            Gx = cc * fma(ddx, dn, sg3 * ldx);
+            Gy = cc * fma(ddy, dn, sg3 * ldy);
+            eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], E);
+            const real cn = cit * nn;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) E[q] = cn * E[q];
             eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gy);
         }
     } else {
-        static_assert(KP == 2 || KP == 4, "velocity lanes: 1, 2 or 4");
+        static_assert(KP == 2 || KP == 4 || KP == 8, "velocity lanes: 1, 2, 4 or 8");
         using Sm = FusedSmem<real, TX, TY, KP>;
         if (active) {
-            // KP = 4: lane 0 ddx, lane 1 ddy, lane 2 ldx + g(u_x), lane 3 ldy + g(u_y)
+            // KP = 8: lanes 0..5 take ddx, ddy, ldx, ldy, E, g(u_y);
+            // KP = 4: lane 0 ddx, lane 1 ddy, lane 2 ldx + E, lane 3 ldy + g(u_y);
             // KP = 2: lane 0 the x parts, lane 1 the y parts
-            const bool lane_x = KP == 2 ? lane_k == 0 : lane_k == 2;
-            const bool lane_y = KP == 2 ? lane_k == 1 : lane_k == 3;
+            const bool lane_ldx = KP == 2 ? lane_k == 0 : lane_k == 2;
+            const bool lane_ldy = KP == 2 ? lane_k == 1 : lane_k == 3;
+            const bool lane_gx = KP == 2 ? lane_k == 0 : (KP == 4 ? lane_k == 2 : lane_k == 4);
+            const bool lane_gy = KP == 2 ? lane_k == 1 : (KP == 4 ? lane_k == 3 : lane_k == 5);
             if (lane_k == 0) {
                 sm.loc[Sm::L_DDX][node] = grad_sum(true);
-                nn = field_val(sm.n[ty + cy][tx + cx]);
-                sm.loc[Sm::L_N][node] = nn;
-                sm.loc[Sm::L_DN][node] = real(g.inv_ds) / nn;
+                sm.loc[Sm::L_DN][node] = real(g.inv_ds) / field_val(sm.n[ty + cy][tx + cx]);
             }
             if (lane_k == 1) sm.loc[Sm::L_DDY][node] = grad_sum(false);
-            if (lane_x) {
-                sm.loc[Sm::L_LDX][node] = glap_sum(true);
-                eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], gx);
+            if (lane_ldx) sm.loc[Sm::L_LDX][node] = glap_sum(true);
+            if (lane_ldy) sm.loc[Sm::L_LDY][node] = glap_sum(false);
+            if (lane_gx) {
+                eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], E);
+                const real cn = cit * field_val(sm.n[ty + cy][tx + cx]);
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) sm.loc[Sm::L_GX + q][node] = gx[q];
+                for (int q = 0; q < NQ; ++q) sm.loc[Sm::L_E + q][node] = cn * E[q];
             }
-            if (lane_y) {
-                sm.loc[Sm::L_LDY][node] = glap_sum(false);
+            if (lane_gy) {
                 eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gy);
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) sm.loc[Sm::L_GY + q][node] = gy[q];
@@ -355,16 +367,15 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
         __syncthreads();
         if (active) {
             const real dn = sm.loc[Sm::L_DN][node];
-            nn = sm.loc[Sm::L_N][node];
-            Fx = fma(sm.loc[Sm::L_DDX][node], dn, sg3 * sm.loc[Sm::L_LDX][node]);
-            Fy = fma(sm.loc[Sm::L_DDY][node], dn, sg3 * sm.loc[Sm::L_LDY][node]);
+            Gx = cc * fma(sm.loc[Sm::L_DDX][node], dn, sg3 * sm.loc[Sm::L_LDX][node]);
+            Gy = cc * fma(sm.loc[Sm::L_DDY][node], dn, sg3 * sm.loc[Sm::L_LDY][node]);
         }
     }
 
     // ---- 5. advection, collision and RK combination, KP velocities at a time
     const int nfx = (TX + 1) * TY, nfy = TX * (TY + 1);
     const long long o = (long long)j * g.pitch + i;
-    const real itau = real(g.inv_tau);
+    const real cf = cb - cit;
     const real cadv = cc * real(g.inv_ds);
     for (int kb = 0; kb < NK; kb += KP) {
         // faces of the KP velocities kb .. kb+KP-1, each computed once and
@@ -425,22 +436,21 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 dy = fma(t.D[k2][q], sm.pop[NQ * k1 + q][r][c], dy);
             }
             const real f = sm.pop[k][r][c];
-            real feq, fxv, fyv;
+            real Ek, gyk;
             if constexpr (KP > 1) {
                 using Sm = FusedSmem<real, TX, TY, KP>;
-                feq = nn * sm.loc[Sm::L_GX + k1][node] * sm.loc[Sm::L_GY + k2][node];
-                fxv = Fx;
-                fyv = Fy;
+                Ek = sm.loc[Sm::L_E + k1][node];
+                gyk = sm.loc[Sm::L_GY + k2][node];
             } else {
-                feq = nn * sel5(gx, k1) * sel5(gy, k2);
-                fxv = Fx;
-                fyv = Fy;
+                Ek = sel5(E, k1);
+                gyk = sel5(gy, k2);
             }
             real adv = 0;
             if (k1 != 2) adv = t.R[k1] * (sm.fx[lane_k][ty][tx + 1] - sm.fx[lane_k][ty][tx]);
             if (k2 != 2) adv = fma(t.R[k2], sm.fy[lane_k][ty + 1][tx] - sm.fy[lane_k][ty][tx], adv);
-            const real Lloc = -fma(fxv, dx, fyv * dy) - (f - feq) * itau;
-            real v = fma(cb, f, fma(cc, Lloc, -cadv * adv));
+            // c L = -c xi.grad f - c F.grad_p f - (c/tau)(f - f^eq) with f^eq = n g g
+            // (Eqs. feq, g_alpha), combined with b f (and a f_n) as in Eq. rk3
+            real v = fma(cf, f, fma(Ek, gyk, -fma(Gx, dx, fma(Gy, dy, cadv * adv))));
             if (ca != real(0)) v = fma(ca, fn[k * g.plane + o], v);
             out[k * g.plane + o] = v;
         }
@@ -462,7 +472,7 @@ constexpr size_t fused_smem_bytes()
 
 // Single grid: one CTA per tile.
 template <typename real, int TX, int TY, int KP, bool LEARNED>
-__global__ void __launch_bounds__(TX *TY *KP)
+__global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT)
 k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
         const __grid_constant__ Geo g, const __grid_constant__ Tab<real> t, real ca, real cb, real cc,
         const float *__restrict__ mlp)
@@ -498,7 +508,7 @@ static_assert(sizeof(BatchRun<double>) % 16 == 0, "BatchRun<double> must be a wh
 static_assert(sizeof(BatchRun<float>) % 16 == 0, "BatchRun<float> must be a whole number of int4 words");
 
 template <typename real, int TX, int TY, int KP>
-__global__ void __launch_bounds__(TX *TY *KP)
+__global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT)
 k_fused_batch(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
               const BatchRun<real> *__restrict__ runs, const int *__restrict__ tile_start, int nruns, int total,
               real ca, real cb, real ccoef)
@@ -544,7 +554,7 @@ cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *sta
                              const Tab<real> &t, StageCoef c, const float *mlp, cudaStream_t s)
 {
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-    k_fused<real, TX, TY, KP, LEARNED><<<grid, TX * TY * KP, fused_smem_bytes<real, TX, TY, KP, LEARNED>(), s>>>(
+    k_fused<real, TX, TY, KP, LEARNED><<<grid, FusedSmem<real, TX, TY, KP>::NT, fused_smem_bytes<real, TX, TY, KP, LEARNED>(), s>>>(
         fs, fn, out, status, g, t, (real)c.ca, (real)c.cb, (real)c.cc, mlp);
     return cudaGetLastError();
 }
@@ -559,14 +569,14 @@ cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, in
     int &per = ctas_per_sm[dev & 63];
     if (per == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per, k_fused_batch<real, TX, TY, KP>, TX * TY * KP, sizeof(FusedSmem<real, TX, TY, KP>));
+            &per, k_fused_batch<real, TX, TY, KP>, FusedSmem<real, TX, TY, KP>::NT, sizeof(FusedSmem<real, TX, TY, KP>));
         if (e != cudaSuccess || per < 1) per = 1;
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = total < per * sms ? total : per * sms;
     if (grid < 1) return cudaSuccess;
-    k_fused_batch<real, TX, TY, KP><<<grid, TX * TY * KP, sizeof(FusedSmem<real, TX, TY, KP>), s>>>(
+    k_fused_batch<real, TX, TY, KP><<<grid, FusedSmem<real, TX, TY, KP>::NT, sizeof(FusedSmem<real, TX, TY, KP>), s>>>(
         fs, fn, out, status, static_cast<const BatchRun<real> *>(runs), tile_start, nruns, total, (real)c.ca,
         (real)c.cb, (real)c.cc);
     return cudaGetLastError();
@@ -577,15 +587,17 @@ cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *sta
                              const Tab<real> &t, StageCoef c, cudaStream_t s)
 {
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-    k_fused<real, TX, TY, KP><<<grid, TX * TY * KP, sizeof(FusedSmem<real, TX, TY, KP>), s>>>(
+    k_fused<real, TX, TY, KP><<<grid, FusedSmem<real, TX, TY, KP>::NT, sizeof(FusedSmem<real, TX, TY, KP>), s>>>(
         fs, fn, out, status, g, t, (real)c.ca, (real)c.cb, (real)c.cc);
     return cudaGetLastError();
 }
 
 // Shapes compiled for each precision: TX x TY nodes per CTA, KP velocities
-// advanced at once (TX*TY*KP threads).  Must match TILE_X/TILE_Y/TILE_K in
+// advanced at once (KP lanes of TX*TY threads rounded up to whole warps).  Must match TILE_X/TILE_Y/TILE_K in
 // olb_internal.cuh.
-#define OLB_FUSED_SHAPE_CASES(real, DO) DO(real, 8, 8, 4) DO(real, 16, 8, 2) DO(real, 16, 8, 1) DO(real, 32, 8, 1) DO(real, 32, 16, 1)
+#define OLB_FUSED_SHAPE_CASES(real, DO) \
+    DO(real, 8, 8, 4) DO(real, 16, 8, 2) DO(real, 16, 8, 1) DO(real, 32, 8, 1) DO(real, 32, 16, 1) DO(real, 8, 8, 8) \
+    DO(real, 7, 8, 8)
 // Shapes with a learned-weights instance (the default shapes of both precisions).
 #define OLB_FUSED_LEARNED_CASES(real, DO) DO(real, 8, 8, 4) DO(real, 16, 8, 2) DO(real, 32, 16, 1)
 #define OLB_FUSED_PREP_CASE(real, A, B, C) \

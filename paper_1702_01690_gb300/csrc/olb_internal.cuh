@@ -81,10 +81,10 @@ OLB_DECLARE_LAUNCHERS(double)
 OLB_DECLARE_LAUNCHERS(float)
 
 // Stage-kernel shapes compiled for both precisions: TX x TY nodes per CTA
-// and KP velocities advanced at once, listed by increasing tile area.
-constexpr int NUM_TILES = 5;
-constexpr int TILE_X[NUM_TILES] = {8, 16, 16, 32, 32};
-constexpr int TILE_Y[NUM_TILES] = {8, 8, 8, 8, 16};
-constexpr int TILE_K[NUM_TILES] = {4, 2, 1, 1, 1};
+// and KP velocities advanced at once.
+constexpr int NUM_TILES = 7;
+constexpr int TILE_X[NUM_TILES] = {8, 16, 16, 32, 32, 8, 7};
+constexpr int TILE_Y[NUM_TILES] = {8, 8, 8, 8, 16, 8, 8};
+constexpr int TILE_K[NUM_TILES] = {4, 2, 1, 1, 1, 8, 8};
 
 }  // namespace olb

@@ -87,22 +87,28 @@ __device__ __forceinline__ double weno5(double v0, double v1, double v2, double 
     const double G2 = fma(2.0, d23, d12);
     const double G3 = fma(4.0, d23, -d34);
     const double p1 = s2 * s3, p2 = s1 * s3, p3 = s1 * s2;
-    const double A1 = p1 * p1, A2 = (6.0 * p2) * p2, A3 = (3.0 * p3) * p3;
-    const double den = A1 + A2 + A3;
-    if (den > 2.3e-308) return fma(fma(A1, G1, fma(A2, G2, A3 * G3)), recip_nr(6.0 * den), v2);
-    double w1, w2, w3;
-    if (s1 == 0.0 || s2 == 0.0 || s3 == 0.0) {
-        w1 = (s1 == 0.0) ? 0.1 : 0.0;
-        w2 = (s2 == 0.0) ? 0.6 : 0.0;
-        w3 = (s3 == 0.0) ? 0.3 : 0.0;
-    } else {
-        const double s = fmin(s1, fmin(s2, s3));
-        const double r1 = s / s1, r2 = s / s2, r3 = s / s3;
-        w1 = 0.1 * r1 * r1;
-        w2 = 0.6 * r2 * r2;
-        w3 = 0.3 * r3 * r3;
+    double A1 = p1 * p1, A2 = (6.0 * p2) * p2, A3 = (3.0 * p3) * p3;
+    double den = A1 + A2 + A3;
+    // den >= 0 (or NaN): its bit pattern orders like its value, so the test
+    // for a normal den runs on the integer pipe
+    if (__double_as_longlong(den) <= 0x0010000000000000LL) {
+        // two or three indicators vanish (Table tab:weno: the ideal weights of
+        // the vanishing set), or the products underflow (min-scaled weights);
+        // only the weights diverge, the combination below is shared
+        if (s1 == 0.0 || s2 == 0.0 || s3 == 0.0) {
+            A1 = (s1 == 0.0) ? 1.0 : 0.0;
+            A2 = (s2 == 0.0) ? 6.0 : 0.0;
+            A3 = (s3 == 0.0) ? 3.0 : 0.0;
+        } else {
+            const double s = fmin(s1, fmin(s2, s3));
+            const double r1 = s / s1, r2 = s / s2, r3 = s / s3;
+            A1 = r1 * r1;
+            A2 = (6.0 * r2) * r2;
+            A3 = (3.0 * r3) * r3;
+        }
+        den = A1 + A2 + A3;
     }
-    return v2 + (w1 * G1 + w2 * G2 + w3 * G3) / (6.0 * (w1 + w2 + w3));
+    return fma(fma(A1, G1, fma(A2, G2, A3 * G3)), recip_nr(6.0 * den), v2);
 }
 
 // FP32 form (same forms and candidates): the products of four squared
