@@ -141,24 +141,31 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
         if (g.walls && (gx < 0 || gx >= g.nx)) continue;
         double n, jx, jy, en;
         if constexpr (sizeof(real) == 8) {
+            // row and column sums of the 5 x 5 populations; the middle root
+            // is 0 (R[2] = R2[2] = 0), so its sums drop out of j and e
             double sx[NQ], sy[NQ];
 #pragma unroll
-            for (int k = 0; k < NQ; ++k) sy[k] = 0.0;
-#pragma unroll
             for (int k1 = 0; k1 < NQ; ++k1) {
-                double s = 0.0;
+                double s = (double)sm.pop[NQ * k1][r][c];
+                if (k1 == 0) sy[0] = s;
+                else sy[0] += s;
 #pragma unroll
-                for (int k2 = 0; k2 < NQ; ++k2) {
+                for (int k2 = 1; k2 < NQ; ++k2) {
                     const double v = (double)sm.pop[NQ * k1 + k2][r][c];
                     s += v;
-                    sy[k2] += v;
+                    if (k1 == 0) sy[k2] = v;
+                    else sy[k2] += v;
                 }
                 sx[k1] = s;
             }
-            n = jx = jy = en = 0.0;
+            n = sx[0];
+            jx = (double)t.R[0] * sx[0];
+            jy = (double)t.R[0] * sy[0];
+            en = (double)t.R2[0] * (sx[0] + sy[0]);
 #pragma unroll
-            for (int k = 0; k < NQ; ++k) {
+            for (int k = 1; k < NQ; ++k) {
                 n += sx[k];
+                if (k == 2) continue;
                 jx = fma((double)t.R[k], sx[k], jx);
                 jy = fma((double)t.R[k], sy[k], jy);
                 en = fma((double)t.R2[k], sx[k] + sy[k], en);
