@@ -65,8 +65,9 @@ enum {
 enum {
     OLB_FP64 = 0,       /* everything in FP64 */
     OLB_FP32_KAHAN = 1  /* populations, fluxes and stencils in FP32; the
-                           25-velocity moment sums Kahan-compensated; T and
-                           Delta p recovered in FP64 */
+                           25-velocity moment sums Kahan-compensated; u, T and
+                           Delta p recovered in double-float (hi + lo FP32)
+                           arithmetic, n and Delta p staged as hi + lo pairs */
 };
 
 /* Non-linear WENO weights. */

@@ -135,11 +135,14 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
 
     // ---- 2. moments at every fluid position of the region that the 7 x 7
     // force stencils reach (columns 1 .. HX-2)
+    const f2 vdw_a = f2_of(g.a), vdw_b = f2_of(g.b);  // FP32 variant only
     for (int e = tid; e < HY * (HX - 2); e += NT) {
         const int r = e / (HX - 2), c = e - r * (HX - 2) + 1;
         const int gx = x0 - 4 + c;
         if (g.walls && (gx < 0 || gx >= g.nx)) continue;
-        double n, jx, jy, en;
+        const int tr = r - 3, tc = c - 4;
+        const bool tile_node = tr >= 0 && tr < TY && tc >= 0 && tc < TX;
+        const bool own = tile_node && x0 + tc < g.nx && y0 + tr < g.ny;
         if constexpr (sizeof(real) == 8) {
             // row and column sums of the 5 x 5 populations; the middle root
             // is 0 (R[2] = R2[2] = 0), so its sums drop out of j and e
@@ -158,10 +161,10 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 }
                 sx[k1] = s;
             }
-            n = sx[0];
-            jx = (double)t.R[0] * sx[0];
-            jy = (double)t.R[0] * sy[0];
-            en = (double)t.R2[0] * (sx[0] + sy[0]);
+            double n = sx[0];
+            double jx = (double)t.R[0] * sx[0];
+            double jy = (double)t.R[0] * sy[0];
+            double en = (double)t.R2[0] * (sx[0] + sy[0]);
 #pragma unroll
             for (int k = 1; k < NQ; ++k) {
                 n += sx[k];
@@ -169,6 +172,23 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 jx = fma((double)t.R[k], sx[k], jx);
                 jy = fma((double)t.R[k], sy[k], jy);
                 en = fma((double)t.R2[k], sx[k] + sy[k], en);
+            }
+            const double inv_n = recip_nr(n);
+            const double ux = jx * inv_n, uy = jy * inv_n;
+            const double T = 0.5 * fma(en, inv_n, -fma(ux, ux, uy * uy));
+            // Delta p = n T - p^w, p^w = n T / (1 - b n) - a n^2 (Eq. vdw)
+            const double nT = n * T;
+            sm.n[r][c] = make_field(n, real(0));
+            sm.dp[r][c] = make_field(nT - fma(nT, recip_nr(1.0 - g.b * n), -g.a * n * n), real(0));
+            if (tile_node) {
+                sm.ux[tr][tc] = (real)ux;
+                sm.uy[tr][tc] = (real)uy;
+                sm.T[tr][tc] = (real)T;
+                if (own) {
+                    const bool ok = (n > 0.0) && (T > 0.0) && (g.b * n < 1.0) && isfinite(n) && isfinite(T) &&
+                                    isfinite(ux) && isfinite(uy);
+                    if (!ok) atomicOr(status, 1);
+                }
             }
         } else {
             Kahan kn{0.f, 0.f}, kx{0.f, 0.f}, ky{0.f, 0.f}, ke{0.f, 0.f};
@@ -182,27 +202,29 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                     ky.add((float)t.R[k2] * v);
                     ke.add(((float)t.R2[k1] + (float)t.R2[k2]) * v);
                 }
-            n = kn.value();
-            jx = kx.value();
-            jy = ky.value();
-            en = ke.value();
-        }
-        const double inv_n = recip_nr(n);
-        const double ux = jx * inv_n, uy = jy * inv_n;
-        const double T = 0.5 * fma(en, inv_n, -fma(ux, ux, uy * uy));
-        // Delta p = n T - p^w, p^w = n T / (1 - b n) - a n^2 (Eq. vdw)
-        const double nT = n * T;
-        sm.n[r][c] = make_field(n, real(0));
-        sm.dp[r][c] = make_field(nT - fma(nT, recip_nr(1.0 - g.b * n), -g.a * n * n), real(0));
-        const int tr = r - 3, tc = c - 4;
-        if (tr >= 0 && tr < TY && tc >= 0 && tc < TX) {
-            sm.ux[tr][tc] = (real)ux;
-            sm.uy[tr][tc] = (real)uy;
-            sm.T[tr][tc] = (real)T;
-            if (x0 + tc < g.nx && y0 + tr < g.ny) {
-                const bool ok = (n > 0.0) && (T > 0.0) && (g.b * n < 1.0) && isfinite(n) && isfinite(T) &&
-                                isfinite(ux) && isfinite(uy);
-                if (!ok) atomicOr(status, 1);
+            // the compensated sums as double-float values; u, T and
+            // Delta p = n T - p^w = n^2 (a - b T / (1 - b n)) (Eq. vdw) in
+            // double-float arithmetic, so that the stencils of n and Delta p
+            // see ~44-bit values without the FP64 pipe
+            const f2 one{1.0f, 0.0f};
+            const f2 N = f2_from_kahan(kn), IN = f2_div(one, N);
+            const f2 UX = f2_mul(f2_from_kahan(kx), IN), UY = f2_mul(f2_from_kahan(ky), IN);
+            const f2 U2 = f2_add(f2_mul(UX, UX), f2_mul(UY, UY));
+            const f2 T = f2_scale(f2_add(f2_mul(f2_from_kahan(ke), IN), f2_neg(U2)), 0.5f);
+            const f2 BN = f2_mul(vdw_b, N);
+            const f2 Q = f2_div(f2_mul(vdw_b, T), f2_add(one, f2_neg(BN)));
+            const f2 DP = f2_mul(f2_mul(N, N), f2_add(vdw_a, f2_neg(Q)));
+            sm.n[r][c] = make_float2(N.hi, N.lo);
+            sm.dp[r][c] = make_float2(DP.hi, DP.lo);
+            if (tile_node) {
+                sm.ux[tr][tc] = UX.hi;
+                sm.uy[tr][tc] = UY.hi;
+                sm.T[tr][tc] = T.hi;
+                if (own) {
+                    const bool ok = (N.hi > 0.0f) && (T.hi > 0.0f) && (BN.hi < 1.0f) && isfinite(N.hi) &&
+                                    isfinite(T.hi) && isfinite(UX.hi) && isfinite(UY.hi);
+                    if (!ok) atomicOr(status, 1);
+                }
             }
         }
     }

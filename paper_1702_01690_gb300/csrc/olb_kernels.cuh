@@ -183,6 +183,60 @@ struct Kahan {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// ---------------------------------------------------------------- double-float
+// A value held as the unevaluated sum hi + lo of two floats (~44 significant
+// bits), built from error-free transformations: Knuth's TwoSum (a + b = s + e
+// exactly), Dekker's Fast2Sum (the same for |a| >= |b|) and the exact product
+// a b = p + e with e = fma(a, b, -p).  Division takes one correction step
+// with the exact residual.  Used for the FP32 variant's moment recovery, so
+// that the low-rate FP64 pipe stays out of the FP32 stage kernel.  Relies on
+// the build's -fmad=false: no product or sum here may be contracted.
+struct f2 {
+    float hi, lo;
+};
+__device__ __forceinline__ f2 two_sum(float a, float b)
+{
+    const float s = a + b, bv = s - a;
+    return {s, (a - (s - bv)) + (b - bv)};
+}
+__device__ __forceinline__ f2 fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ f2 f2_from_kahan(const Kahan &k) { return fast_two_sum(k.s, -k.c); }
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    // both parts summed exactly, then renormalised (accurate under cancellation)
+    f2 s = two_sum(a.hi, b.hi);
+    const f2 t = two_sum(a.lo, b.lo);
+    s = fast_two_sum(s.hi, s.lo + t.hi);
+    return fast_two_sum(s.hi, s.lo + t.lo);
+}
+__device__ __forceinline__ f2 f2_neg(f2 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p);
+    return fast_two_sum(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ f2 f2_scale(f2 a, float s) { return {a.hi * s, a.lo * s}; }  // s a power of 2
+__device__ __forceinline__ f2 f2_div(f2 a, f2 b)
+{
+    const float r = __frcp_rn(b.hi);
+    const float q1 = a.hi * r;
+    // residual a - b q1 (b.hi q1 exactly by fma), then q2 = residual / b
+    const float p = b.hi * q1;
+    const float pe = fmaf(b.hi, q1, -p);
+    const f2 res = f2_add(a, f2_neg(fast_two_sum(p, fmaf(b.lo, q1, pe))));
+    return fast_two_sum(q1, res.hi * r);
+}
+__device__ __forceinline__ f2 f2_of(double v)
+{
+    const float hi = __double2float_rn(v);
+    return {hi, __double2float_rn(v - (double)hi)};
+}
+
 // Moments of the 25 populations at one node in FP64: n, jx, jy, e.
 template <typename real>
 __device__ __forceinline__ void node_sums(const real *__restrict__ f, long long plane, long long o,
