@@ -298,12 +298,14 @@ def run_ours(args, rank, world):
     t0 = time.perf_counter()
     for _ in range(e2e_iters):
         ctx.init_fields(*[h.numpy() for h in host_in])
-        ctx.step(1)
+        ctx.step_async(1)  # olb_moments synchronises; the status word is sticky
         olb._check(olb.library().olb_moments(ctx.handle, *[olb._VP(h.data_ptr()) for h in host_out]), "olb_moments")
     e2e_s = (time.perf_counter() - t0) / e2e_iters
+    if ctx.status() != 0:
+        raise RuntimeError("e2e: step status")
     e2e = {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N * 8,
            "d2h_bytes_per_step": 4 * N * 8,
-           "what": "olb_init_fields (host, pinned) + olb_step(1) + olb_moments (host, pinned) per step"}
+           "what": "olb_init_fields (host, pinned) + olb_step_async(1) + olb_moments (host, pinned) per step"}
     ctx.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

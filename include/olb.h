@@ -126,7 +126,9 @@ void olb_destroy(olb_ctx *ctx);
 /* Set f = f^eq(n, u, T) at every node (Eq. feq) from host fields [ny][nx]
  * and reset the status word.  Rejects non-finite values, n <= 0,
  * b n >= 1 and T <= 0 with OLB_ERR_ARG before touching the device.
- * Returns after the device work is complete. */
+ * Page-locked (pinned) host arrays are read by the kernel directly, other
+ * host memory through a staging copy; either way the call returns after the
+ * device work is complete and the caller keeps ownership of the arrays. */
 int olb_init_fields(olb_ctx *ctx, const double *n, const double *ux,
                     const double *uy, const double *T);
 
@@ -152,7 +154,9 @@ int olb_get_status(olb_ctx *ctx);
 
 /* Moments n, u_x, u_y, T of the current populations (Sec. 2.2; T from the
  * trace of Eq. sigmaq_def) into host arrays [ny][nx].  Any argument may be
- * NULL to skip it.  Returns after the copies are complete. */
+ * NULL to skip it.  Page-locked (pinned) host arrays are written by the
+ * kernel directly, others through a staging copy.  Returns after the values
+ * are in the host arrays. */
 int olb_moments(olb_ctx *ctx, double *n, double *ux, double *uy, double *T);
 
 /* As olb_moments into device arrays (FP64, [ny][nx]), enqueued on the

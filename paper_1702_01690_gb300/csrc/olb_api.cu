@@ -415,22 +415,50 @@ static int init_from_device(olb_ctx *c, const double *n, const double *ux, const
     return OLB_OK;
 }
 
+// Host fields admissible as an initial state: n > 0, b n < 1, T > 0, all
+// finite (NaN fails every comparison).  One pass without early exits.
+static bool fields_admissible(const double *n, const double *ux, const double *uy, const double *T, size_t N,
+                              double b)
+{
+    const double inf = HUGE_VAL;
+    int ok = 1;
+    for (size_t q = 0; q < N; ++q)
+        ok &= (n[q] > 0.0) & (n[q] < inf) & (b * n[q] < 1.0) & (T[q] > 0.0) & (T[q] < inf) & (ux[q] > -inf) &
+              (ux[q] < inf) & (uy[q] > -inf) & (uy[q] < inf);
+    return ok != 0;
+}
+
+// Device address of page-locked (pinned, mapped) host memory, which kernels
+// read and write directly; nullptr for anything else (pageable memory takes
+// a staging copy).
+static void *mapped_view(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 extern "C" int olb_init_fields(olb_ctx *c, const double *n, const double *ux, const double *uy, const double *T)
 {
     if (!c || !n || !ux || !uy || !T) return OLB_ERR_ARG;
     const size_t N = (size_t)c->geo.nx * c->geo.ny;
-    for (size_t q = 0; q < N; ++q) {
-        if (!std::isfinite(n[q]) || !std::isfinite(ux[q]) || !std::isfinite(uy[q]) || !std::isfinite(T[q]))
-            return OLB_ERR_ARG;
-        if (!(n[q] > 0.0) || !(T[q] > 0.0) || !(c->p.b * n[q] < 1.0)) return OLB_ERR_ARG;
-    }
+    if (!fields_admissible(n, ux, uy, T, N, c->p.b)) return OLB_ERR_ARG;
     DeviceGuard dg(c->device);
     const double *src[4] = {n, ux, uy, T};
+    const double *dev[4];
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
-        e = cudaMemcpyAsync(c->stage4 + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+        dev[k] = static_cast<const double *>(mapped_view(src[k]));
+        if (!dev[k]) {
+            e = cudaMemcpyAsync(c->stage4 + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+            dev[k] = c->stage4 + k * N;
+        }
+    }
     if (e != cudaSuccess) return cuda_status(e);
-    int r = init_from_device(c, c->stage4, c->stage4 + N, c->stage4 + 2 * N, c->stage4 + 3 * N);
+    int r = init_from_device(c, dev[0], dev[1], dev[2], dev[3]);
     if (r != OLB_OK) return r;
     return cuda_status(cudaStreamSynchronize(c->stream));
 }
@@ -505,14 +533,22 @@ extern "C" int olb_moments(olb_ctx *c, double *n, double *ux, double *uy, double
     if (!c->initialized) return OLB_ERR_STATE;
     DeviceGuard dg(c->device);
     const size_t N = (size_t)c->geo.nx * c->geo.ny;
-    double *dev[4] = {c->stage4, c->stage4 + N, c->stage4 + 2 * N, c->stage4 + 3 * N};
     double *host[4] = {n, ux, uy, T};
-    int r = moments_device(c, host[0] ? dev[0] : nullptr, host[1] ? dev[1] : nullptr,
-                           host[2] ? dev[2] : nullptr, host[3] ? dev[3] : nullptr);
+    double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool staged[4] = {false, false, false, false};
+    for (int k = 0; k < 4; ++k) {
+        if (!host[k]) continue;
+        dev[k] = static_cast<double *>(mapped_view(host[k]));
+        if (!dev[k]) {
+            dev[k] = c->stage4 + k * N;
+            staged[k] = true;
+        }
+    }
+    int r = moments_device(c, dev[0], dev[1], dev[2], dev[3]);
     if (r != OLB_OK) return r;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
-        if (host[k]) e = cudaMemcpyAsync(host[k], dev[k], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (staged[k]) e = cudaMemcpyAsync(host[k], dev[k], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return cuda_status(e);
 }

@@ -152,6 +152,35 @@ def test_device_entry_points(olb):
     assert max(moments_rel(mh, o.moments()).values()) < FP64_TOL
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pinned_host_buffers_match_pageable(olb, precision):
+    """Pinned host arrays (read and written by the kernels directly) give the
+    same state and moments, bit for bit, as pageable ones (staging copies);
+    NULL skips a moment; invalid pinned input is still rejected."""
+    import torch
+    p, fl = inputs.shear_64x4()
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in fl]
+    a = olb.create(p, precision)
+    b = olb.create(p, precision)
+    a.init_fields(*fl)
+    olb._check(olb.library().olb_init_fields(b.handle, *[olb._VP(t.data_ptr()) for t in pinned]), "init")
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    a.step(5)
+    b.step(5)
+    out = [torch.zeros((p.ny, p.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    ptrs = [olb._VP(t.data_ptr()) for t in out]
+    ptrs[2] = None
+    olb._check(olb.library().olb_moments(b.handle, *ptrs), "moments")
+    ma = a.moments()
+    for k in (0, 1, 3):
+        assert np.array_equal(out[k].numpy(), ma[k])
+    assert not out[2].numpy().any()
+    bad = [t.clone().pin_memory() for t in pinned]
+    bad[3][0, 0] = -1.0
+    rc = olb.library().olb_init_fields(b.handle, *[olb._VP(t.data_ptr()) for t in bad])
+    assert rc == olb.ERR_ARG
+
+
 def test_diverged_state_reported(olb):
     """A state with negative density is reported as OLB_ERR_DIVERGED by the
     status word, never as a device fault."""
