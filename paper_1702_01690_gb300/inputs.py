@@ -188,6 +188,26 @@ def planar_walls(nx: int = 1024, ny: int = 8, steps: int = 20000) -> tuple:
     return p, cold_rest(nx, ny, ds, SEED_BASE + 1, 1.0, 0.01, 1.0)
 
 
+def planar_tanh(nx: int = 320, Tw: float = 0.9, dt: float = 2e-4, steps: int = 100000) -> tuple:
+    """Liquid slabs at the diffuse walls x = 0, 1 and vapour in the middle
+    (ny = 1, periodic y), the full-channel form of the paper's half-channel
+    planar set-up (Sec. 4): n = n_g + (n_l - n_g)/2 [1 + tanh((|x - 1/2| -
+    1/4) / xi)] (Eq. tanh, interfaces at 1/4 and 3/4), Maxwell densities at
+    T = T_w, xi = sqrt(8 sigma / (9 (1 - T_w))) (Eq. xiwagner, sigma for its
+    kappa), T = T_w, u = 0, tau = 0.005, sigma = 1e-4; ds = 1/320 and
+    dt = 2e-4 as in the paper's planar runs."""
+    ds = 1.0 / nx
+    ng, nl = MAXWELL[round(Tw, 6)]
+    sigma = 1e-4
+    xi = math.sqrt(8.0 * sigma / (9.0 * (1.0 - Tw)))
+    x = node_x(nx, ds)
+    n = ng + 0.5 * (nl - ng) * (1.0 + np.tanh((np.abs(x - 0.5) - 0.25) / xi))
+    p = RunParams(nx=nx, ny=1, ds=ds, dt=dt, tau=0.005, sigma=sigma, Tw=(Tw, Tw), side_x=1, steps=steps,
+                  name=f"planar tanh interfaces {nx}x1 diffuse walls Tw={Tw}")
+    z = np.zeros((1, nx))
+    return p, (n[None, :].copy(), z, z.copy(), np.full((1, nx), float(Tw)))
+
+
 def laplace(n: int = 2048, R: float = 0.2, steps: int = 5000) -> tuple:
     """Laplace drop on an n x n periodic grid, T = 0.9, tanh width 0.02,
     dt = 2.5e-6 (2048 / n)^2 (capillary limit, 2-D omega dt ~ 0.7; CFL 0.015
