@@ -19,6 +19,7 @@
  *       stencil_glap) with the field reflection rule (Sec. 3.4.3)
  *     force F (Eq. F_def)
  *     diffuse-wall density n_w (Eqs. diffuse_flux, nw; Sec. 3.4.2)
+ *     ghost populations of specular sides (Sec. 3.4.1) and diffuse walls
  *     WENO-5 fluxes (Eqs. weno5_flux, weno5_omega, weno5_delta,
  *       weno5_sigma, Table tab:weno)
  *     momentum-space derivative (Eq. derf), equilibrium (Eqs. feq, g_alpha)
@@ -38,8 +39,13 @@
  *   R5  the left wall is the mirror image of the right wall of Sec. 3.4.2.
  *   R6  the numerator of Eq. nw is the WENO flux at the wall face built
  *       with the extrapolated ghosts; the flux includes the factor p/m.
- *   R7  field reflection is even about the wall face; periodic sides wrap
- *       modulo the grid size (which may be smaller than the stencil).
+ *   R7  field reflection is even about the wall or specular face (a double
+ *       reflection at corners); periodic sides wrap modulo the grid size
+ *       (which may be smaller than the stencil).
+ *   R13 specular reflection, written for the bottom and left sides only,
+ *       applies to the top and right sides as their mirror image; x and y
+ *       sides are specular or periodic independently, and a specular x = 0
+ *       side may face a diffuse wall at x = nx ds (the paper's half channel).
  *   R8  T = (sum |p|^2 f / n - |u|^2) / 2 (D = 2, m = 1).
  *
  * Units: m = 1 (Sec. 2.1).  Node (i, j), 0-based, sits at
@@ -371,9 +377,17 @@ typedef struct orc_params {
     double ds, dt, tau;
     double a, b, sigma;
     double Tw[2], uw[2];   /* [0] left wall (x = 0), [1] right wall (x = 1) */
-    int side_x;            /* 0 periodic, 1 diffuse walls on both x sides */
-    int side_y;            /* 0 periodic */
+    int side_x;            /* 0 periodic, 1 diffuse walls on both x sides,
+                              2 specular on both x sides, 3 specular at
+                              x = 0 and a diffuse wall at x = nx ds */
+    int side_y;            /* 0 periodic, 2 specular on both y sides */
 } orc_params;
+
+/* Kind of one side: 0 periodic, 1 diffuse wall, 2 specular reflection. */
+enum { SIDE_PERIODIC = 0, SIDE_DIFFUSE = 1, SIDE_SPECULAR = 2 };
+
+static int side_lo_x(const orc_params *p) { return p->side_x == 3 ? SIDE_SPECULAR : p->side_x; }
+static int side_hi_x(const orc_params *p) { return p->side_x == 3 ? SIDE_DIFFUSE : p->side_x; }
 
 typedef struct orc_ctx {
     orc_params p;
@@ -408,7 +422,9 @@ orc_ctx *orc_create(const orc_params *p)
 {
     init_constants();
     if (p->nx < 1 || p->ny < 1) return NULL;
-    if (p->side_x == 1 && p->nx < 3) return NULL;
+    if (p->side_x < 0 || p->side_x > 3 || (p->side_y != 0 && p->side_y != 2)) return NULL;
+    if (p->side_x != 0 && p->nx < 3) return NULL;
+    if (p->side_y != 0 && p->ny < 3) return NULL;
     orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
     c->p = *p;
     c->N = (size_t)p->nx * (size_t)p->ny;
@@ -442,20 +458,39 @@ orc_ctx *orc_create(const orc_params *p)
     return c;
 }
 
-/* Population kappa at x-index i (possibly a ghost) and row j of array fs.
- * Ghost values for diffuse walls (Sec. 3.4.2): outgoing velocities take the
- * quadratic extrapolation, incoming ones f^eq_w = n_w g g; values no flux
- * ever reads are NaN so that an accidental use shows up. */
+/* Population kappa at x-index i and row j (either possibly a ghost) of
+ * array fs.  Periodic sides wrap.  Specular sides (Sec. 3.4.1): the ghost at
+ * distance m from the side takes the population of the velocity with the
+ * normal component reversed at the m-th node inside (k1 -> 4 - k1 across an
+ * x side, k2 -> 4 - k2 across a y side).  Diffuse walls (Sec. 3.4.2):
+ * outgoing velocities take the quadratic extrapolation, incoming ones
+ * f^eq_w = n_w g g.  Values no flux ever reads are NaN so that an accidental
+ * use shows up. */
 static double fval(const orc_ctx *c, const double *fs, int kap, int i, int j)
 {
-    int nx = c->p.nx;
-    j = wrap(j, c->p.ny);
+    int nx = c->p.nx, ny = c->p.ny;
+    if (j < 0 || j >= ny) {
+        if (c->p.side_y == SIDE_SPECULAR) {
+            int m = j < 0 ? -1 - j : j - ny;
+            if (m > 2) return NAN;
+            j = j < 0 ? -1 - j : 2 * ny - 1 - j;
+            kap = Q * (kap / Q) + (Q - 1 - kap % Q);
+        } else {
+            j = wrap(j, ny);
+        }
+    }
     if (i >= 0 && i < nx) return fs[((size_t)j * nx + i) * K + kap];
-    if (c->p.side_x == 0) return fs[((size_t)j * nx + wrap(i, nx)) * K + kap];
+    int side = i < 0 ? side_lo_x(&c->p) : side_hi_x(&c->p);
+    int m = i < 0 ? -1 - i : i - nx;  /* ghost layer 0, 1, 2 */
+    if (side == SIDE_PERIODIC) return fs[((size_t)j * nx + wrap(i, nx)) * K + kap];
+    if (side == SIDE_SPECULAR) {
+        if (m > 2) return NAN;
+        int im = i < 0 ? -1 - i : 2 * nx - 1 - i;
+        return fs[((size_t)j * nx + im) * K + Q * (Q - 1 - kap / Q) + kap % Q];
+    }
     int k1 = kap / Q;
     double px = g_R[k1];
-    if (i >= nx) {  /* right wall, ghost layer m = 0, 1, 2 */
-        int m = i - nx;
+    if (i >= nx) {  /* right wall */
         if (px > 0.0) {
             double a0 = fs[((size_t)j * nx + nx - 1) * K + kap];
             double a1 = fs[((size_t)j * nx + nx - 2) * K + kap];
@@ -464,10 +499,9 @@ static double fval(const orc_ctx *c, const double *fs, int kap, int i, int j)
             if (m == 1) return 6.0 * a0 - 8.0 * a1 + 3.0 * a2;
             return NAN;
         }
-        if (px < 0.0) return c->nw[1 * c->p.ny + j] * c->geqw[1][kap];
+        if (px < 0.0) return c->nw[1 * ny + j] * c->geqw[1][kap];
         return NAN;
-    } else {        /* left wall, ghost layer m = 0, 1, 2 at i = -1, -2, -3 */
-        int m = -1 - i;
+    } else {        /* left wall, ghost layer m at i = -1 - m */
         if (px < 0.0) {
             double a0 = fs[((size_t)j * nx + 0) * K + kap];
             double a1 = fs[((size_t)j * nx + 1) * K + kap];
@@ -476,7 +510,7 @@ static double fval(const orc_ctx *c, const double *fs, int kap, int i, int j)
             if (m == 1) return 6.0 * a0 - 8.0 * a1 + 3.0 * a2;
             return NAN;
         }
-        if (px > 0.0) return c->nw[0 * c->p.ny + j] * c->geqw[0][kap];
+        if (px > 0.0) return c->nw[0 * ny + j] * c->geqw[0][kap];
         return NAN;
     }
 }
@@ -497,16 +531,15 @@ static double flux_x(const orc_ctx *c, const double *fs, int kap, int i, int j)
     return px * (c->learned ? orc_weno5_learned(c->mlp, v, NULL) : orc_weno5(v, NULL));
 }
 
-/* y-flux at the face y = j ds between rows j-1 and j (y always periodic). */
+/* y-flux at the face y = j ds between rows j-1 and j. */
 static double flux_y(const orc_ctx *c, const double *fs, int kap, int i, int j)
 {
     double py = g_R[kap % Q];
-    int nx = c->p.nx, ny = c->p.ny;
     double v[5];
     if (py > 0.0) {
-        for (int q = 0; q < 5; ++q) v[q] = fs[((size_t)wrap(j - 3 + q, ny) * nx + i) * K + kap];
+        for (int q = 0; q < 5; ++q) v[q] = fval(c, fs, kap, i, j - 3 + q);
     } else if (py < 0.0) {
-        for (int q = 0; q < 5; ++q) v[q] = fs[((size_t)wrap(j + 2 - q, ny) * nx + i) * K + kap];
+        for (int q = 0; q < 5; ++q) v[q] = fval(c, fs, kap, i, j + 2 - q);
     } else {
         return 0.0;
     }
@@ -514,17 +547,15 @@ static double flux_y(const orc_ctx *c, const double *fs, int kap, int i, int j)
 }
 
 /* Field value with the boundary rule of Sec. 3.4.3: even reflection about
- * a wall face, periodic wrap otherwise. */
+ * a wall or specular side (a double reflection at corners), periodic wrap
+ * otherwise. */
 static double field_at(const orc_ctx *c, const double *fld, int i, int j)
 {
-    int nx = c->p.nx;
-    if (c->p.side_x == 1) {
-        if (i < 0) i = -1 - i;
-        else if (i >= nx) i = 2 * nx - 1 - i;
-    } else {
-        i = wrap(i, nx);
-    }
-    j = wrap(j, c->p.ny);
+    int nx = c->p.nx, ny = c->p.ny;
+    if (i < 0) i = side_lo_x(&c->p) == SIDE_PERIODIC ? wrap(i, nx) : -1 - i;
+    else if (i >= nx) i = side_hi_x(&c->p) == SIDE_PERIODIC ? wrap(i, nx) : 2 * nx - 1 - i;
+    if (j < 0) j = c->p.side_y == SIDE_SPECULAR ? -1 - j : wrap(j, ny);
+    else if (j >= ny) j = c->p.side_y == SIDE_SPECULAR ? 2 * ny - 1 - j : wrap(j, ny);
     return fld[(size_t)j * nx + i];
 }
 
@@ -568,15 +599,17 @@ static void stage_fields(orc_ctx *c, const double *fs)
         c->Fx[q] = (gx / ds) / c->n[q] + p->sigma * (lx / ds3);
         c->Fy[q] = (gy / ds) / c->n[q] + p->sigma * (ly / ds3);
     }
-    if (p->side_x == 1) {
-        for (int j = 0; j < ny; ++j) {
+    for (int j = 0; j < ny; ++j) {
+        if (side_hi_x(p) == SIDE_DIFFUSE) {
             /* right wall: outgoing p_x > 0, face x = nx ds */
             double num = 0.0;
             for (int kap = 0; kap < K; ++kap)
                 if (g_R[kap / Q] > 0.0) num += flux_x(c, fs, kap, nx, j);
             c->nw[1 * ny + j] = -num / c->denw[1];
+        }
+        if (side_lo_x(p) == SIDE_DIFFUSE) {
             /* left wall: outgoing p_x < 0, face x = 0 */
-            num = 0.0;
+            double num = 0.0;
             for (int kap = 0; kap < K; ++kap)
                 if (g_R[kap / Q] < 0.0) num += flux_x(c, fs, kap, 0, j);
             c->nw[0 * ny + j] = -num / c->denw[0];
