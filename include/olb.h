@@ -12,8 +12,9 @@
  *                            stencils of Sec. 3.3)
  *          -(f - f^eq)/tau  (Eqs. evolution, feq)
  *
- * and combines the stages as in Eq. rk3.  Sides normal to x are periodic or
- * diffuse-reflection walls (Sec. 3.4.2); y is periodic.
+ * and combines the stages as in Eq. rk3.  Sides normal to x are periodic,
+ * diffuse-reflection walls (Sec. 3.4.2) or specular-reflection planes
+ * (Sec. 3.4.1); sides normal to y are periodic or specular.
  *
  * Conventions
  *  - Every call returns an int status: OLB_OK (0) or a negative OLB_ERR_*.
@@ -54,11 +55,20 @@ enum {
     OLB_ERR_NOMEM = -7     /* device allocation failed */
 };
 
-/* Boundary kinds of the sides normal to x (side_x) and y (side_y). */
+/* Boundary kinds of the sides normal to x (side_x) and y (side_y).  A
+ * specular side (Sec. 3.4.1) is a mirror plane: its three ghost layers hold
+ * the populations of the first three nodes inside with the normal velocity
+ * component reversed; n and Delta p are reflected evenly at walls and
+ * specular sides alike, with a double reflection at corners (Sec. 3.4.3). */
 enum {
-    OLB_SIDE_PERIODIC = 0, /* wrap modulo the grid size */
-    OLB_SIDE_DIFFUSE = 1   /* diffuse-reflection walls at x = 0 and x = nx ds
-                              (Sec. 3.4.2); only valid for side_x */
+    OLB_SIDE_PERIODIC = 0,         /* wrap modulo the grid size */
+    OLB_SIDE_DIFFUSE = 1,          /* diffuse-reflection walls at x = 0 and
+                                      x = nx ds (Sec. 3.4.2); side_x only */
+    OLB_SIDE_SPECULAR = 2,         /* specular reflection on both sides */
+    OLB_SIDE_SPECULAR_DIFFUSE = 3  /* specular at x = 0, diffuse wall at
+                                      x = nx ds (the half channel of Sec. 4,
+                                      the reduced Laplace domain of Sec. 5);
+                                      side_x only */
 };
 
 /* Arithmetic of the populations. */
@@ -82,17 +92,20 @@ enum {
 /* Problem statement (Sec. 2, Sec. 3).  Walls: index 0 is the wall at x = 0,
  * index 1 the wall at x = nx ds. */
 typedef struct olb_params {
-    int nx, ny;         /* nodes along x and y, >= 1 (>= 3 along x with walls) */
+    int nx, ny;         /* nodes along x and y, >= 1 (>= 3 along an axis
+                           whose sides are walls or specular) */
     double ds;          /* lattice spacing delta s > 0 (Sec. 2.1) */
     double dt;          /* time step delta t > 0 (Sec. 3.1) */
     double tau;         /* relaxation time tau > 0, constant (Eq. evolution) */
     double a, b;        /* van der Waals p^w = n T / (1 - b n) - a n^2;
                            a = 9/8, b = 1/3 is Eq. vdw; a = b = 0 is the ideal gas */
     double sigma;       /* surface-tension parameter of Eq. F_def, >= 0 */
-    double Tw[2];       /* wall temperatures T_w > 0 (used with OLB_SIDE_DIFFUSE) */
+    double Tw[2];       /* wall temperatures T_w > 0 at x = 0 and x = nx ds
+                           (used at diffuse walls) */
     double uw[2];       /* tangential (y) wall velocities u_w */
-    int side_x;         /* OLB_SIDE_PERIODIC or OLB_SIDE_DIFFUSE */
-    int side_y;         /* OLB_SIDE_PERIODIC */
+    int side_x;         /* OLB_SIDE_PERIODIC, _DIFFUSE, _SPECULAR or
+                           _SPECULAR_DIFFUSE */
+    int side_y;         /* OLB_SIDE_PERIODIC or OLB_SIDE_SPECULAR */
     int precision;      /* OLB_FP64 or OLB_FP32_KAHAN */
     int weno_mode;      /* OLB_WENO_JS or OLB_WENO_LEARNED */
 } olb_params;

@@ -252,13 +252,24 @@ extern "C" const char *olb_status_string(int status)
     }
 }
 
+void olb::set_sides(Geo *g, const olb_params *p)
+{
+    g->walls = p->side_x != OLB_SIDE_PERIODIC;
+    g->wall_lo = p->side_x == OLB_SIDE_DIFFUSE;
+    g->wall_hi = p->side_x == OLB_SIDE_DIFFUSE || p->side_x == OLB_SIDE_SPECULAR_DIFFUSE;
+    g->spec_lo = p->side_x == OLB_SIDE_SPECULAR || p->side_x == OLB_SIDE_SPECULAR_DIFFUSE;
+    g->spec_hi = p->side_x == OLB_SIDE_SPECULAR;
+    g->spec_y = p->side_y == OLB_SIDE_SPECULAR;
+}
+
 int olb::validate_params(const olb_params *p)
 {
     if (!p) return OLB_ERR_ARG;
     if (p->nx < 1 || p->ny < 1) return OLB_ERR_ARG;
-    if (p->side_x != OLB_SIDE_PERIODIC && p->side_x != OLB_SIDE_DIFFUSE) return OLB_ERR_ARG;
-    if (p->side_y != OLB_SIDE_PERIODIC) return OLB_ERR_ARG;
-    if (p->side_x == OLB_SIDE_DIFFUSE && p->nx < 3) return OLB_ERR_ARG;
+    if (p->side_x < OLB_SIDE_PERIODIC || p->side_x > OLB_SIDE_SPECULAR_DIFFUSE) return OLB_ERR_ARG;
+    if (p->side_y != OLB_SIDE_PERIODIC && p->side_y != OLB_SIDE_SPECULAR) return OLB_ERR_ARG;
+    if (p->side_x != OLB_SIDE_PERIODIC && p->nx < 3) return OLB_ERR_ARG;
+    if (p->side_y != OLB_SIDE_PERIODIC && p->ny < 3) return OLB_ERR_ARG;
     if (p->precision != OLB_FP64 && p->precision != OLB_FP32_KAHAN) return OLB_ERR_ARG;
     if (p->weno_mode != OLB_WENO_JS && p->weno_mode != OLB_WENO_LEARNED) return OLB_ERR_ARG;
     if (!(p->ds > 0.0) || !(p->dt > 0.0) || !(p->tau > 0.0)) return OLB_ERR_ARG;
@@ -266,9 +277,10 @@ int olb::validate_params(const olb_params *p)
     if (!(p->sigma >= 0.0) || !(p->b >= 0.0) || !std::isfinite(p->a) || !std::isfinite(p->sigma) ||
         !std::isfinite(p->b))
         return OLB_ERR_ARG;
-    if (p->side_x == OLB_SIDE_DIFFUSE)
-        for (int s = 0; s < 2; ++s)
-            if (!(p->Tw[s] > 0.0) || !std::isfinite(p->Tw[s]) || !std::isfinite(p->uw[s])) return OLB_ERR_ARG;
+    for (int s = 0; s < 2; ++s) {
+        const bool wall = p->side_x == OLB_SIDE_DIFFUSE || (s == 1 && p->side_x == OLB_SIDE_SPECULAR_DIFFUSE);
+        if (wall && (!(p->Tw[s] > 0.0) || !std::isfinite(p->Tw[s]) || !std::isfinite(p->uw[s]))) return OLB_ERR_ARG;
+    }
     if ((long long)p->nx * p->ny > (1LL << 31) / 32) return OLB_ERR_ARG;
     const double pmax = std::sqrt(5.0 + std::sqrt(10.0));
     if (!(pmax * p->dt / p->ds < 1.0)) return OLB_ERR_CFL;
@@ -335,7 +347,7 @@ extern "C" int olb_create(const olb_params *p, void *stream, olb_ctx **out)
     g.ny = p->ny;
     g.pitch = (p->nx + 31) / 32 * 32;
     g.plane = (long long)g.pitch * g.ny;
-    g.walls = p->side_x == OLB_SIDE_DIFFUSE;
+    set_sides(&g, p);
     g.ds = p->ds;
     g.inv_ds = 1.0 / p->ds;
     g.inv_ds3 = 1.0 / (p->ds * p->ds * p->ds);

@@ -202,7 +202,7 @@ extern "C" int olb_batch_create(const olb_params *runs, int count, void *stream,
         g.ny = p->ny;
         g.pitch = (p->nx + 31) / 32 * 32;
         g.plane = (long long)g.pitch * g.ny;
-        g.walls = p->side_x == OLB_SIDE_DIFFUSE;
+        set_sides(&g, p);
         g.ds = p->ds;
         g.inv_ds = 1.0 / p->ds;
         g.inv_ds3 = 1.0 / (p->ds * p->ds * p->ds);
@@ -456,7 +456,9 @@ extern "C" int olb_batch_autotune(olb_batch *b, int nsteps, int *tx, int *ty, in
     BDevice dg(b->device);
     std::string sig = std::to_string(b->precision) + ":" + std::to_string(b->device);
     for (int r = 0; r < b->count; ++r)
-        sig += ";" + std::to_string(b->geo[r].nx) + "x" + std::to_string(b->geo[r].ny) + (b->geo[r].walls ? "w" : "p");
+        sig += ";" + std::to_string(b->geo[r].nx) + "x" + std::to_string(b->geo[r].ny) + (b->geo[r].walls ? "w" : "p") +
+               std::to_string(b->geo[r].wall_lo * 8 + b->geo[r].wall_hi * 4 + b->geo[r].spec_lo * 2 + b->geo[r].spec_hi) +
+               (b->geo[r].spec_y ? "s" : "");
     int best = -1;
     {
         std::lock_guard<std::mutex> guard(g_tune_lock);

@@ -116,19 +116,52 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     const bool active = (node < NN) && (i < g.nx) && (j < g.ny);
 
     // ---- 1. populations of the region (c <-> x = x0 - 4 + c, r <-> y = y0 - 3 + r)
+    //    Periodic sides wrap.  Ghost layers 0..2 of a specular side hold the
+    //    populations of the first three nodes inside with the normal
+    //    velocity component reversed (Sec. 3.4.1); diffuse-wall ghosts are
+    //    set in phase 3; anything further out is never read and holds 0.
     for (int e = tid; e < HY * HX; e += NT) {
         const int r = e / HX, c = e - r * HX;
-        const int gy = wrap(y0 - 3 + r, g.ny);
-        int gx = x0 - 4 + c;
-        const bool inside = gx >= 0 && gx < g.nx;
-        if (!g.walls) gx = wrap(gx, g.nx);
-        if (inside || !g.walls) {
-            const real *src = fs + (long long)gy * g.pitch + gx;
+        int gy = y0 - 3 + r, gx = x0 - 4 + c;
+        bool flip_x = false, flip_y = false, zero = false;
+        if (gy < 0 || gy >= g.ny) {
+            if (!g.spec_y) {
+                gy = wrap(gy, g.ny);
+            } else if ((gy < 0 ? -1 - gy : gy - g.ny) <= 2) {
+                gy = gy < 0 ? -1 - gy : 2 * g.ny - 1 - gy;
+                flip_y = true;
+            } else {
+                zero = true;
+            }
+        }
+        if (gx < 0 || gx >= g.nx) {
+            const bool lo = gx < 0;
+            if (!g.walls) {
+                gx = wrap(gx, g.nx);
+            } else if ((lo ? g.spec_lo : g.spec_hi) && (lo ? -1 - gx : gx - g.nx) <= 2) {
+                gx = lo ? -1 - gx : 2 * g.nx - 1 - gx;
+                flip_x = true;
+            } else {
+                zero = true;
+            }
+        }
+        if (zero) {
+#pragma unroll 5
+            for (int k = 0; k < NK; ++k) sm.pop[k][r][c] = real(0);
+            continue;
+        }
+        const real *src = fs + (long long)gy * g.pitch + gx;
+        if (!flip_x && !flip_y) {
 #pragma unroll 5
             for (int k = 0; k < NK; ++k) sm.pop[k][r][c] = __ldg(src + k * g.plane);
         } else {
-#pragma unroll 5
-            for (int k = 0; k < NK; ++k) sm.pop[k][r][c] = real(0);
+#pragma unroll
+            for (int k1 = 0; k1 < NQ; ++k1)
+#pragma unroll
+                for (int k2 = 0; k2 < NQ; ++k2) {
+                    const int kk = NQ * (flip_x ? NQ - 1 - k1 : k1) + (flip_y ? NQ - 1 - k2 : k2);
+                    sm.pop[NQ * k1 + k2][r][c] = __ldg(src + kk * g.plane);
+                }
         }
     }
     __syncthreads();
@@ -136,10 +169,13 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     // ---- 2. moments at every fluid position of the region that the 7 x 7
     // force stencils reach (columns 1 .. HX-2)
     const f2 vdw_a = f2_of(g.a), vdw_b = f2_of(g.b);  // FP32 variant only
+    // (ghost positions of walls and specular sides take the reflected fields
+    // in phase 3)
     for (int e = tid; e < HY * (HX - 2); e += NT) {
         const int r = e / (HX - 2), c = e - r * (HX - 2) + 1;
-        const int gx = x0 - 4 + c;
+        const int gx = x0 - 4 + c, gyr = y0 - 3 + r;
         if (g.walls && (gx < 0 || gx >= g.nx)) continue;
+        if (g.spec_y && (gyr < 0 || gyr >= g.ny)) continue;
         const int tr = r - 3, tc = c - 4;
         const bool tile_node = tr >= 0 && tr < TY && tc >= 0 && tc < TX;
         const bool own = tile_node && x0 + tc < g.nx && y0 + tr < g.ny;
@@ -229,12 +265,28 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
         }
     }
 
-    // ---- 3. diffuse walls
-    const bool left_wall = g.walls && x0 == 0;
-    const bool right_wall = g.walls && (x0 + TX + 3 >= g.nx);
-    if (left_wall || right_wall) {
+    // ---- 3. sides: n and Delta p reflected evenly into the ghost layers of
+    // walls and specular planes (Sec. 3.4.3; y first, then x over every row,
+    // which makes the corners a double reflection), then the diffuse walls
+    const bool x_lo = g.walls && x0 == 0;                // ghost columns at x = 0
+    const bool x_hi = g.walls && (x0 + TX + 3 >= g.nx);  // ghost columns at x = nx ds
+    const bool left_wall = x_lo && g.wall_lo;
+    const bool right_wall = x_hi && g.wall_hi;
+    if (g.spec_y && (y0 == 0 || y0 + TY + 2 >= g.ny)) {
         __syncthreads();
-        // mirror the fields, extrapolate the outgoing populations
+        for (int e = tid; e < HY * HX; e += NT) {
+            const int r = e / HX, c = e - r * HX;
+            const int gyr = y0 - 3 + r;
+            if (gyr >= 0 && gyr < g.ny) continue;
+            if ((gyr < 0 ? -1 - gyr : gyr - g.ny) > 2) continue;
+            const int rm = (gyr < 0 ? -1 - gyr : 2 * g.ny - 1 - gyr) - (y0 - 3);
+            sm.n[r][c] = sm.n[rm][c];
+            sm.dp[r][c] = sm.dp[rm][c];
+        }
+    }
+    if (x_lo || x_hi) {
+        __syncthreads();
+        // mirror the fields; at diffuse walls extrapolate the outgoing populations
         for (int e = tid; e < HY * HX; e += NT) {
             const int r = e / HX, c = e - r * HX;
             const int gx = x0 - 4 + c;
@@ -246,7 +298,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             const int cm = mirror - (x0 - 4);
             sm.n[r][c] = sm.n[r][cm];
             sm.dp[r][c] = sm.dp[r][cm];
-            if (m > 1) continue;
+            if (m > 1 || !(right ? g.wall_hi : g.wall_lo)) continue;
             // nearest three fluid nodes, nearest first
             const int c0 = right ? g.nx - 1 - (x0 - 4) : 0 - (x0 - 4);
             const int dc = right ? -1 : 1;
@@ -263,6 +315,8 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 }
             }
         }
+    }
+    if (left_wall || right_wall) {
         // wall densities of the tile rows: one warp per (wall, row), lanes
         // 0..9 take the outgoing velocities, the wall-face flux with inline
         // extrapolated ghosts, reduced by shuffles
@@ -294,7 +348,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             if (gx >= 0 && gx < g.nx) continue;
             const bool right = gx >= g.nx;
             const int m = right ? gx - g.nx : -1 - gx;
-            if (m > 2) continue;
+            if (m > 2 || !(right ? right_wall : left_wall)) continue;
             const real nwv = sm.nw[right ? 1 : 0][tr];
 #pragma unroll
             for (int k1 = 0; k1 < NQ; ++k1) {

@@ -22,7 +22,10 @@ constexpr int NK = 25;  // velocities
 // Geometry and physical parameters, passed by value to every kernel.
 struct Geo {
     int nx, ny, pitch;
-    int walls;           // 1: diffuse walls at x = 0 and x = nx ds
+    int walls;           // 1: the x sides are not periodic (walls or specular)
+    int wall_lo, wall_hi;  // diffuse wall at x = 0 / at x = nx ds (Sec. 3.4.2)
+    int spec_lo, spec_hi;  // specular plane at x = 0 / at x = nx ds (Sec. 3.4.1)
+    int spec_y;            // specular planes at y = 0 and y = ny ds
     long long plane;     // pitch * ny
     double ds, inv_ds, inv_ds3, dt, inv_tau, sigma, a, b;
 };
@@ -51,6 +54,7 @@ void fill_tab(Tab<real> *tab, const HostTables &h, const double Tw[2], const dou
 // Parameter validation of olb_create (OLB_OK / OLB_ERR_ARG / OLB_ERR_CFL)
 // and the mapping of CUDA errors to status codes (olb_api.cu).
 int validate_params(const ::olb_params *p);
+void set_sides(Geo *g, const ::olb_params *p);
 int cuda_status(cudaError_t e);
 
 // RK-3 stage coefficients: out = ca f^n + cb f_s + cc L[f_s] (Eq. rk3).

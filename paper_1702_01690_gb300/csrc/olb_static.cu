@@ -94,7 +94,7 @@ extern "C" int olb_step_static(const olb_params *p, void *stream, double *f, int
     g.ny = p->ny;
     g.pitch = p->nx;  // the caller's [25][ny][nx] layout, no padding
     g.plane = (long long)g.nx * g.ny;
-    g.walls = p->side_x == OLB_SIDE_DIFFUSE;
+    set_sides(&g, p);
     g.ds = p->ds;
     g.inv_ds = 1.0 / p->ds;
     g.inv_ds3 = 1.0 / (p->ds * p->ds * p->ds);

@@ -22,7 +22,7 @@ _lib = ctypes.CDLL(LIB)
 
 OK = 0
 ERR_ARG, ERR_CFL, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_STATE, ERR_NOMEM = -1, -2, -3, -4, -5, -6, -7
-SIDE_PERIODIC, SIDE_DIFFUSE = 0, 1
+SIDE_PERIODIC, SIDE_DIFFUSE, SIDE_SPECULAR, SIDE_SPECULAR_DIFFUSE = 0, 1, 2, 3
 FP64, FP32_KAHAN = 0, 1
 WENO_JS, WENO_LEARNED = 0, 1
 MLP_PARAMS = 1347

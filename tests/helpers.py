@@ -86,3 +86,28 @@ def check_against_envelope(m_gpu, p, fields, steps, rtol=1e-11, factor=10.0):
         allowed = max(rtol * s, factor * float(np.max(e)))
         out[name] = float(np.max(np.abs(np.asarray(g) - r) / allowed))
     return out
+
+
+def symmetric_fields(nx, ny, sym_x, sym_y, seed):
+    """Smooth random fields, even (n, T, the tangential velocity) or odd (the
+    normal velocity) under i -> nx-1-i (sym_x) and j -> ny-1-j (sym_y)."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, y)
+
+    def smooth(amp):
+        a = rng.uniform(-1, 1, 4)
+        return amp * (a[0] * np.cos(2 * np.pi * X + a[1]) * np.cos(2 * np.pi * Y + a[2])
+                      + a[3] * np.sin(4 * np.pi * X + a[2]) * np.sin(2 * np.pi * Y + a[1]))
+
+    n = 1.0 + smooth(0.05)
+    ux, uy = smooth(0.02), smooth(0.02)
+    T = 0.95 + smooth(0.02)
+    if sym_x:
+        n, T, uy = [(v + v[:, ::-1]) / 2 for v in (n, T, uy)]
+        ux = (ux - ux[:, ::-1]) / 2
+    if sym_y:
+        n, T, ux = [(v + v[::-1, :]) / 2 for v in (n, T, ux)]
+        uy = (uy - uy[::-1, :]) / 2
+    return n, ux, uy, T

@@ -25,6 +25,15 @@ def test_every_declared_symbol_is_exported(olb):
     assert set(olb.SYMBOLS) == set(names)
 
 
+def test_side_enum_matches_header(olb):
+    import re
+    from pathlib import Path
+    text = (Path(__file__).resolve().parents[1] / "include" / "olb.h").read_text()
+    vals = {m.group(1): int(m.group(2)) for m in re.finditer(r"OLB_SIDE_(\w+) = (\d+)", text)}
+    assert vals == {"PERIODIC": olb.SIDE_PERIODIC, "DIFFUSE": olb.SIDE_DIFFUSE, "SPECULAR": olb.SIDE_SPECULAR,
+                    "SPECULAR_DIFFUSE": olb.SIDE_SPECULAR_DIFFUSE}
+
+
 def test_params_struct_layout_matches_header(olb):
     # 2 ints, 6 doubles, 2+2 doubles, 4 ints (with natural alignment)
     assert ctypes.sizeof(olb.Params) == 8 + 6 * 8 + 4 * 8 + 4 * 4
@@ -47,6 +56,8 @@ def _params(olb, **kw):
     (dict(dt=-1.0), -1), (dict(tau=0.0), -1), (dict(sigma=-1e-4), -1),
     (dict(side_x=7), -1), (dict(side_y=1), -1), (dict(precision=9), -1),
     (dict(weno_mode=3), -1), (dict(Tw=(0.0, 0.9)), -1), (dict(b=-0.1), -1),
+    (dict(side_x=4), -1), (dict(side_y=3), -1), (dict(side_x=2, nx=2), -1), (dict(side_y=2, ny=2), -1),
+    (dict(side_x=3, Tw=(0.9, 0.0)), -1),
     (dict(dt=1.0 / 64 / 2.8), -2), (dict(dt=0.1, ds=1.0), -2), (dict(dt=0.02, tau=0.005, ds=0.5), -2),
 ])
 def test_create_rejects_invalid_params(olb, kw, code):

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1702_01690_gb300 import inputs
+from helpers import symmetric_fields
 
 TOL = 1e-12
 
@@ -20,31 +20,6 @@ def run(nx, ny, fields, steps, side_x, side_y, ds, dt=2e-4):
     o.init_fields(*fields)
     o.step(steps)
     return o.get_populations(), o
-
-
-def symmetric_fields(nx, ny, sym_x, sym_y, seed):
-    """Smooth random fields, even (n, T, the tangential velocity) or odd (the
-    normal velocity) under i -> nx-1-i (sym_x) and j -> ny-1-j (sym_y)."""
-    rng = np.random.default_rng(seed)
-    x = (np.arange(nx) + 0.5) / nx
-    y = (np.arange(ny) + 0.5) / ny
-    X, Y = np.meshgrid(x, y)
-
-    def smooth(amp):
-        a = rng.uniform(-1, 1, 4)
-        return amp * (a[0] * np.cos(2 * np.pi * X + a[1]) * np.cos(2 * np.pi * Y + a[2])
-                      + a[3] * np.sin(4 * np.pi * X + a[2]) * np.sin(2 * np.pi * Y + a[1]))
-
-    n = 1.0 + smooth(0.05)
-    ux, uy = smooth(0.02), smooth(0.02)
-    T = 0.95 + smooth(0.02)
-    if sym_x:
-        n, T, uy = [(v + v[:, ::-1]) / 2 for v in (n, T, uy)]
-        ux = (ux - ux[:, ::-1]) / 2
-    if sym_y:
-        n, T, ux = [(v + v[::-1, :]) / 2 for v in (n, T, ux)]
-        uy = (uy - uy[::-1, :]) / 2
-    return n, ux, uy, T
 
 
 def rel(a, b):
