@@ -25,8 +25,7 @@
  *     momentum-space derivative (Eq. derf), equilibrium (Eqs. feq, g_alpha)
  *     L[f] (Eq. ecast) and the Shu-Osher combination.
  *
- * Readings of points the paper leaves open (each one is listed in the
- * design notes of the repository):
+ * Readings of points the paper leaves open:
  *   R1  gradient-of-Laplacian coefficients c1, c4 are misprinted; this file
  *       uses c1 = -17/2160, c4 = -59/540, the unique values that make the
  *       stencil 4th-order exact and reproduce the paper's 1-D reduction
