@@ -11,6 +11,9 @@ experiments:
   planar walls    n = 1 + 0.01 noise, T = 1, diffuse walls   (Sec. 7 noise
                   at x = 0, 1                                recipe, Sec. 4 walls)
   Laplace drop    tanh drop of radius R, vapour outside      (Sec. 5)
+  planar tanh     liquid slabs at the walls, Eq. tanh       (Sec. 4)
+  Laplace bubble  gas bubble in the reduced (specular-sided) (Sec. 5)
+                  domain
   phase separation between cold plates                      (Sec. 7)
 
 Noise.  The paper draws U(-0.01, 0.01) per node on a grid of 320 nodes per
@@ -65,8 +68,8 @@ class RunParams:
     sigma: float = 1e-4
     Tw: tuple = (1.0, 1.0)
     uw: tuple = (0.0, 0.0)
-    side_x: int = 0     # 0 periodic, 1 diffuse walls
-    side_y: int = 0
+    side_x: int = 0     # 0 periodic, 1 diffuse walls, 2 specular, 3 specular x = 0 + diffuse wall x = 1
+    side_y: int = 0     # 0 periodic, 2 specular
     steps: int = 1
     name: str = ""
 
@@ -188,17 +191,16 @@ def planar_walls(nx: int = 1024, ny: int = 8, steps: int = 20000) -> tuple:
     return p, cold_rest(nx, ny, ds, SEED_BASE + 1, 1.0, 0.01, 1.0)
 
 
-def planar_tanh(nx: int = 320, Tw: float = 0.9, dt: float = 2e-4, steps: int = 100000) -> tuple:
+def planar_tanh(nx: int = 320, Tw: float = 0.9, dt: float = 2e-4, steps: int = 100000, sigma: float = 1e-4) -> tuple:
     """Liquid slabs at the diffuse walls x = 0, 1 and vapour in the middle
     (ny = 1, periodic y), the full-channel form of the paper's half-channel
     planar set-up (Sec. 4): n = n_g + (n_l - n_g)/2 [1 + tanh((|x - 1/2| -
     1/4) / xi)] (Eq. tanh, interfaces at 1/4 and 3/4), Maxwell densities at
     T = T_w, xi = sqrt(8 sigma / (9 (1 - T_w))) (Eq. xiwagner, sigma for its
-    kappa), T = T_w, u = 0, tau = 0.005, sigma = 1e-4; ds = 1/320 and
-    dt = 2e-4 as in the paper's planar runs."""
+    kappa), T = T_w, u = 0, tau = 0.005; ds = 1/320 and dt = 2e-4 as in the
+    paper's planar runs."""
     ds = 1.0 / nx
     ng, nl = MAXWELL[round(Tw, 6)]
-    sigma = 1e-4
     xi = math.sqrt(8.0 * sigma / (9.0 * (1.0 - Tw)))
     x = node_x(nx, ds)
     n = ng + 0.5 * (nl - ng) * (1.0 + np.tanh((np.abs(x - 0.5) - 0.25) / xi))
@@ -206,6 +208,26 @@ def planar_tanh(nx: int = 320, Tw: float = 0.9, dt: float = 2e-4, steps: int = 1
                   name=f"planar tanh interfaces {nx}x1 diffuse walls Tw={Tw}")
     z = np.zeros((1, nx))
     return p, (n[None, :].copy(), z, z.copy(), np.full((1, nx), float(Tw)))
+
+
+def laplace_bubble_quarter(R: float, sigma: float = 1e-4, Tw: float = 0.8, n: int = 160) -> tuple:
+    """The paper's reduced Laplace domain (Sec. 5): x, y in [0, 1/2] with the
+    channel centre at (0, 0), specular bottom, left and top sides and a
+    diffuse wall at x = 1/2 (T_w); ds = 1/320, dt = 2e-4, tau = 5e-3.  A gas
+    bubble of radius R centred at (0, 0): n = n_g + (n_l - n_g)/2 [1 +
+    tanh((r - R) / xi)] with the Maxwell densities at T_w and xi of
+    Eq. xiwagner, T = T_w, u = 0."""
+    ds = 0.5 / n
+    ng, nl = MAXWELL[round(Tw, 6)]
+    xi = math.sqrt(8.0 * sigma / (9.0 * (1.0 - Tw)))
+    x = node_x(n, ds)
+    X, Y = np.meshgrid(x, x)
+    r = np.sqrt(X ** 2 + Y ** 2)
+    dens = ng + 0.5 * (nl - ng) * (1.0 + np.tanh((r - R) / xi))
+    p = RunParams(nx=n, ny=n, ds=ds, dt=2e-4, tau=5e-3, sigma=sigma, Tw=(Tw, Tw), side_x=3, side_y=2,
+                  name=f"Laplace bubble R={R} quarter domain {n}^2")
+    z = np.zeros((n, n))
+    return p, (dens, z, z.copy(), np.full((n, n), float(Tw)))
 
 
 def laplace(n: int = 2048, R: float = 0.2, steps: int = 5000) -> tuple:
