@@ -122,3 +122,71 @@ def test_laplace_law_on_reduced_domain(olb):
     print(f"gamma_Lap {slope:.6e} (paper {g_lap:.6e}, gamma_pl {g_pl:.6e}); intercept {intercept:.2e}")
     assert abs(slope / g_lap - 1) < 0.02 and abs(slope / g_pl - 1) < 0.02
     assert abs(intercept) < 0.01 * max(jump)
+
+
+def _fit_nu(t, a, u0, nu0):
+    """nu of the least-squares fit of a(t) = u0 exp(-nu t) with u0 fixed (Eq.
+    shear_sol): root of sum t e^{-nu t} (a - u0 e^{-nu t}) by bisection."""
+    g = lambda nu: np.sum(t * np.exp(-nu * t) * (a - u0 * np.exp(-nu * t)))
+    lo, hi = 0.5 * nu0, 1.5 * nu0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if (g(lo) > 0) == (g(mid) > 0):
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_shear_wave_galilean_tables_match_paper(olb):
+    """Sec. 6.1: shear waves of the ideal gas (T0 = 0.8, tau = 5e-4, dt = 2e-4,
+    u0 = 1e-3) on N = 20..60 nodes at background velocities V = 0, 0.1, ...,
+    0.5, 1, 2, all 40 runs advanced together as one batch for 2e5 steps, the
+    amplitude projected on sin k(x - V t) every 1000 steps (Eq. shear_ut).
+    eta_app from the least-squares fit of Eq. shear_sol with u0 fixed, L2 of
+    Eq. shear_L2.  The exponents in dx of eta_app/eta_0 - 1 and of L2 (Table
+    tab:shear_ux) and in V of their differences from V = 0 (Table
+    tab:shear_nx, fitted over V = 0.1..0.5) agree with the paper's to 1e-3
+    (measured to 1e-5)."""
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))[
+        "shear_wave_exponents"]
+    T0, tau, dt, u0 = 0.8, 5e-4, 2e-4, 1e-3
+    Ns = gold["V_order_N"]
+    Vs = [0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 1.0, 2.0]
+    runs, fields, keys = [], [], []
+    for V in Vs:
+        for N in Ns:
+            runs.append(inputs.RunParams(nx=N, ny=1, ds=1.0 / N, dt=dt, tau=tau, a=0.0, b=0.0))
+            fields.append(inputs.shear_wave(N, 1, 1.0 / N, 1.0, T0, u0, V=V))
+            keys.append((V, N))
+    b = olb.Batch(runs)
+    for k, f in enumerate(fields):
+        b.init_fields(k, *f)
+    S, chunk, kw = 200, 1000, 2.0 * math.pi
+    amps = np.zeros((len(runs), S))
+    for s in range(S):
+        assert b.step(chunk) == 0
+        t = (s + 1) * chunk * dt
+        for r, (V, N) in enumerate(keys):
+            x = inputs.node_x(N, 1.0 / N)
+            amps[r, s] = 2.0 / N * np.sum(b.moments(r)[2][0] * np.sin(kw * (x - V * t)))
+    ts = np.arange(1, S + 1) * chunk * dt
+    nu_an = kw ** 2 * tau * T0  # Eq. shear_sol: eta_0 / rho_0 = tau T0
+    f = np.ones(S + 1)
+    f[0] = f[-1] = 0.5
+    eta, L2 = {}, {}
+    for r, key in enumerate(keys):
+        eta[key] = _fit_nu(ts, amps[r], u0, nu_an) / nu_an
+        ratio = np.concatenate([[u0], amps[r]]) / (u0 * np.exp(-nu_an * np.concatenate([[0.0], ts]))) - 1.0
+        L2[key] = math.sqrt(np.sum(f * ratio ** 2) / S)
+    for V, e_ref, l_ref in zip(gold["dx_order_V"], gold["dx_order_eta"], gold["dx_order_L2"]):
+        e_ord = -np.polyfit(np.log(Ns), np.log([abs(eta[(V, N)] - 1) for N in Ns]), 1)[0]
+        l_ord = -np.polyfit(np.log(Ns), np.log([L2[(V, N)] for N in Ns]), 1)[0]
+        print(f"V {V}: dx order eta {e_ord:.6f} (paper {e_ref}), L2 {l_ord:.6f} (paper {l_ref})")
+        assert abs(e_ord - e_ref) < 1e-3 and abs(l_ord - l_ref) < 1e-3
+    small = Vs[1:6]
+    for N, e_ref, l_ref in zip(Ns, gold["V_order_eta"], gold["V_order_L2"]):
+        e_ord = np.polyfit(np.log(small), np.log([abs(eta[(V, N)] - eta[(0.0, N)]) for V in small]), 1)[0]
+        l_ord = np.polyfit(np.log(small), np.log([abs(L2[(V, N)] - L2[(0.0, N)]) for V in small]), 1)[0]
+        print(f"N {N}: V order eta {e_ord:.6f} (paper {e_ref}), L2 {l_ord:.6f} (paper {l_ref})")
+        assert abs(e_ord - e_ref) < 1e-3 and abs(l_ord - l_ref) < 1e-3
