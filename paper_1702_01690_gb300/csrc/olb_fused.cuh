@@ -334,7 +334,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 const real a2 = sm.pop[k][tr + 3][c0 + 2 * dc];
                 const real g0 = fma(real(3), a0 - a1, a2);
                 const real g1 = fma(real(6), a0, fma(real(-8), a1, real(3) * a2));
-                flux = t.R[k1] * weno5(a2, a1, a0, g0, g1);
+                flux = t.R[k1] * face_value<real, LEARNED>(mlp, a2, a1, a0, g0, g1);
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) flux += __shfl_xor_sync(0xffffffffu, flux, off);

@@ -131,6 +131,7 @@ def test_learned_stage_matches_oracle(olb, trained, precision):
     o.set_mlp(theta.astype(np.float64))
     o.step(5)
     err = moments_rel(ctx.moments(), o.moments())
+    print("learned stage vs oracle", precision, err)
     if precision == 0:
         assert max(err.values()) < 1e-6, err
     else:
