@@ -202,6 +202,33 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ ranks
+def rank_barrier():
+    """Barrier over the ranks of the default process group (none without one)."""
+    import torch.distributed as tdist
+    if tdist.is_available() and tdist.is_initialized() and tdist.get_world_size() > 1:
+        tdist.barrier()
+
+
+def max_over_ranks(value: float) -> float:
+    """Largest value over the ranks of the default process group (a CPU
+    tensor for gloo, a CUDA tensor for NCCL); the value itself without one."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, nodes: int, steps: int, ms: float) -> float:
+    """Whole-job node-updates/s: every rank advanced `nodes` nodes `steps`
+    times in the slowest rank's `ms` milliseconds."""
+    return world * nodes * steps / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ GPU leg
 def time_steps(ctx, steps, warmup, flush, stream):
     import torch
@@ -226,9 +253,6 @@ def run_ours(args, rank, world):
     import torch
     from paper_1702_01690_gb300 import olb
 
-    dist = world > 1
-    if dist:
-        import torch.distributed as tdist
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
@@ -240,19 +264,15 @@ def run_ours(args, rank, world):
 
     ctx = olb.create(p, olb.FP64, stream)
     ctx.init_fields(*dev_fields)
-    if dist:
-        tdist.barrier()
     torch.cuda.synchronize()
+    rank_barrier()
     with ClockSampler(local) as clk:
         total_ms, _ = time_steps(ctx, args.steps, args.warmup, flush, stream)
     torch.cuda.synchronize()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        tdist.barrier()
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    rank_barrier()
+    total_ms = max_over_ranks(total_ms)
     ms_step = total_ms / args.steps
-    value = world * N * args.steps / (total_ms / 1e3)
+    value = job_value(world, N, args.steps, total_ms)
     m64 = ctx.moments()
 
     # dominant kernel: per-launch device time of each kernel kind
@@ -272,7 +292,11 @@ def run_ours(args, rank, world):
     # FP32 + Kahan variant on the same workload
     ctx32 = olb.create(p, olb.FP32_KAHAN, stream)
     ctx32.init_fields(*dev_fields)
+    torch.cuda.synchronize()
+    rank_barrier()
     total32, _ = time_steps(ctx32, args.steps, args.warmup, flush, stream)
+    rank_barrier()
+    total32 = max_over_ranks(total32)
     m32 = ctx32.moments()
     prof32 = ctx32.profile(max(3, min(args.steps, 50)))
     ach32 = STAGE_FLOPS_PER_NODE_FP32 * N / (prof32["stage_ms"] * 1e-3) / 1e12
@@ -281,7 +305,7 @@ def run_ours(args, rank, world):
     err32 = {"n": float(np.max(np.abs(m32[0] - m64[0])) / np.max(np.abs(m64[0]))),
              "u": float(max(np.max(np.abs(m32[1] - m64[1])), np.max(np.abs(m32[2] - m64[2]))) / us),
              "T": float(np.max(np.abs(m32[3] - m64[3])) / np.max(np.abs(m64[3])))}
-    v32 = world * N * args.steps / (total32 / 1e3)
+    v32 = job_value(world, N, args.steps, total32)
     fp32 = {"value": v32, "ms_per_step": total32 / args.steps, "speedup_vs_fp64": v32 / value,
             "max_rel_err_vs_fp64_after_steps": err32, "steps_compared": args.warmup + args.steps,
             "roofline": {"kernel": f"k_fused<float,{tile32[0]},{tile32[1]},{tile32[2]}>", "bound": "alu", "achieved": ach32,
@@ -295,15 +319,18 @@ def run_ours(args, rank, world):
     e2e_iters = max(3, min(args.steps, 50))
     ctx.init_fields(*[h.numpy() for h in host_in])
     torch.cuda.synchronize()
+    rank_barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_iters):
         ctx.init_fields(*[h.numpy() for h in host_in])
         ctx.step_async(1)  # olb_moments synchronises; the status word is sticky
         olb._check(olb.library().olb_moments(ctx.handle, *[olb._VP(h.data_ptr()) for h in host_out]), "olb_moments")
     e2e_s = (time.perf_counter() - t0) / e2e_iters
+    rank_barrier()
+    e2e_s = max_over_ranks(e2e_s)
     if ctx.status() != 0:
         raise RuntimeError("e2e: step status")
-    e2e = {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N * 8,
+    e2e = {"value": job_value(world, N, 1, 1e3 * e2e_s), "unit": UNIT, "h2d_bytes_per_step": 4 * N * 8,
            "d2h_bytes_per_step": 4 * N * 8,
            "what": "olb_init_fields (host, pinned) + olb_step_async(1) + olb_moments (host, pinned) per step"}
     ctx.close()
@@ -344,13 +371,15 @@ def run_batch(args, rank, world):
         shape = b.autotune(2)
         b.step(args.warmup)
         torch.cuda.synchronize()
+        rank_barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             e0.record(stream)
             b.step_async(args.steps)
             e1.record(stream)
             torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        rank_barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1))
         rc, _ = b.status()
         if rc != 0:
             raise RuntimeError(f"batch diverged ({name})")
@@ -358,7 +387,7 @@ def run_batch(args, rank, world):
         flops = (STAGE_FLOPS_PER_NODE if prec == olb.FP64 else STAGE_FLOPS_PER_NODE_FP32) * nodes
         peak = PEAK_FP64_TFLOPS if prec == olb.FP64 else PEAK_FP32_TFLOPS
         ach = flops / (stage_ms * 1e-3) / 1e12
-        out[name] = {"value": world * nodes * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+        out[name] = {"value": job_value(world, nodes, args.steps, ms), "ms_per_step": ms / args.steps,
                      "shape": list(shape), "stage_ms": stage_ms,
                      "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                                   "frac": ach / peak}, "clocks": clk.summary()}
