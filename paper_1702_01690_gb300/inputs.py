@@ -191,16 +191,17 @@ def planar_walls(nx: int = 1024, ny: int = 8, steps: int = 20000) -> tuple:
     return p, cold_rest(nx, ny, ds, SEED_BASE + 1, 1.0, 0.01, 1.0)
 
 
-def planar_tanh(nx: int = 320, Tw: float = 0.9, dt: float = 2e-4, steps: int = 100000, sigma: float = 1e-4) -> tuple:
+def planar_tanh(nx: int = 320, Tw: float = 0.9, dt: float = 2e-4, steps: int = 100000, sigma: float = 1e-4,
+                densities=None) -> tuple:
     """Liquid slabs at the diffuse walls x = 0, 1 and vapour in the middle
     (ny = 1, periodic y), the full-channel form of the paper's half-channel
     planar set-up (Sec. 4): n = n_g + (n_l - n_g)/2 [1 + tanh((|x - 1/2| -
     1/4) / xi)] (Eq. tanh, interfaces at 1/4 and 3/4), Maxwell densities at
     T = T_w, xi = sqrt(8 sigma / (9 (1 - T_w))) (Eq. xiwagner, sigma for its
     kappa), T = T_w, u = 0, tau = 0.005; ds = 1/320 and dt = 2e-4 as in the
-    paper's planar runs."""
+    paper's planar runs.  `densities` = (n_g, n_l) for a T_w outside MAXWELL."""
     ds = 1.0 / nx
-    ng, nl = MAXWELL[round(Tw, 6)]
+    ng, nl = densities if densities is not None else MAXWELL[round(Tw, 6)]
     xi = math.sqrt(8.0 * sigma / (9.0 * (1.0 - Tw)))
     x = node_x(nx, ds)
     n = ng + 0.5 * (nl - ng) * (1.0 + np.tanh((np.abs(x - 0.5) - 0.25) / xi))
