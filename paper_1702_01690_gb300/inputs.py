@@ -14,6 +14,8 @@ experiments:
   planar tanh     liquid slabs at the walls, Eq. tanh       (Sec. 4)
   Laplace bubble  gas bubble in the reduced (specular-sided) (Sec. 5)
                   domain
+  moving bubble   the same bubble carried at u_y = V between  (Sec. 6.3)
+                  a specular side and a moving wall
   phase separation between cold plates                      (Sec. 7)
 
 Noise.  The paper draws U(-0.01, 0.01) per node on a grid of 320 nodes per
@@ -229,6 +231,25 @@ def laplace_bubble_quarter(R: float, sigma: float = 1e-4, Tw: float = 0.8, n: in
                   name=f"Laplace bubble R={R} quarter domain {n}^2")
     z = np.zeros((n, n))
     return p, (dens, z, z.copy(), np.full((n, n), float(Tw)))
+
+
+def moving_bubble(V: float, R: float = 0.25, sigma: float = 1e-4, Tw: float = 0.8) -> tuple:
+    """The moving-bubble set-up of Sec. 6.3: x in [0, 1/2] with a specular
+    side at x = 0 and a diffuse wall at x = 1/2 (T_w, moving along y at
+    u_w = V), periodic y over a unit length (y in [-1/2, 1/2)); a gas bubble
+    of radius R centred at (0, 0) (Eq. tanh, Maxwell densities at T_w, xi of
+    Eq. xiwagner), T = T_w and u_y = V everywhere; ds = 1/320, dt = 2e-4,
+    tau = 5e-3.  Node y-coordinates of the returned fields are
+    node_y(ny, ds) - 1/2."""
+    ds = 1.0 / 320
+    nx, ny = 160, 320
+    ng, nl = MAXWELL[round(Tw, 6)]
+    xi = math.sqrt(8.0 * sigma / (9.0 * (1.0 - Tw)))
+    X, Y = np.meshgrid(node_x(nx, ds), node_y(ny, ds) - 0.5)
+    n = ng + 0.5 * (nl - ng) * (1.0 + np.tanh((np.sqrt(X ** 2 + Y ** 2) - R) / xi))
+    p = RunParams(nx=nx, ny=ny, ds=ds, dt=2e-4, tau=5e-3, sigma=sigma, Tw=(Tw, Tw), uw=(V, V), side_x=3, side_y=0,
+                  name=f"moving bubble V={V}")
+    return p, (n, np.zeros_like(n), np.full_like(n, float(V)), np.full_like(n, float(Tw)))
 
 
 def laplace(n: int = 2048, R: float = 0.2, steps: int = 5000) -> tuple:
