@@ -220,7 +220,7 @@ def test_moving_bubble_is_galilean_invariant(olb):
     V = 0, 0.01, 0.02, 0.05, 0.1 advanced together as one batch (FP32 +
     Kahan variant).  Over 20 <= t <= 30 the Laplace-law surface tension
     gamma = R_f (p^w_in - p^w_out) differs from the resting bubble's by well
-    below 1 % (the paper: well below 1 %; measured <= 1.2e-3), and the
+    below 1 % (the paper reports under 1 %; measured <= 1.2e-3), and the
     bubble centre trails the advected position V t only slightly (the paper:
     it lags; measured 1.0 % .. 0.6 % of V t at t = 30), the lag growing with
     V."""
@@ -278,8 +278,8 @@ def test_longitudinal_waves_match_linear_theory(olb):
     the van der Waals phases).  With P_eta = p^w and P_kappa = p^i in Eq.
     long_coeff the sound speeds are the paper's 1.130 (vapour) and 2.056
     (liquid); the fitted c_s matches them within 1e-4 (measured <= 5e-5);
-    nu_a converges at order 3.8..5.2 over N = 20..30 (the paper: between 4
-    and 5) to within 2e-2 at N = 60 (measured <= 1e-2); the nu_a shift from
+    nu_a converges at order 3.8..5.2 over N = 20..30 (the paper finds 4 to
+    5) to within 2e-2 at N = 60 (measured <= 1e-2); the nu_a shift from
     V = 0 grows like V^2 (order within 0.1 of 2; Table tab:long_errnx:
     1.96..1.99 at N = 60, measured 1.98..2.00)."""
     from scipy.optimize import curve_fit
