@@ -168,11 +168,10 @@ static bool is_fp64(const olb_ctx *c) { return c->p.precision == OLB_FP64; }
 //   f1 = f + dt L[f];  f2 = 3/4 f + 1/4 f1 + 1/4 dt L[f1];
 //   f  = 1/3 f + 2/3 f2 + 2/3 dt L[f2]  (written in place: f is read only at
 //   the node being written).
-static const double *stage_coef(double dt, int st, StageCoef *c)
+static StageCoef stage_coef(double dt, int st)
 {
     const StageCoef coef[3] = {{0.0, 1.0, dt}, {0.75, 0.25, 0.25 * dt}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt}};
-    *c = coef[st];
-    return nullptr;
+    return coef[st];
 }
 
 template <typename real>
@@ -188,8 +187,7 @@ static cudaError_t enqueue_stage(olb_ctx *c, int st, cudaStream_t s)
     real *f0 = (real *)c->f[0], *f1 = (real *)c->f[1], *f2 = (real *)c->f[2];
     const real *src[3] = {f0, f1, f2};
     real *dst[3] = {f1, f2, f0};
-    StageCoef coef;
-    stage_coef(c->p.dt, st, &coef);
+    const StageCoef coef = stage_coef(c->p.dt, st);
     return launch_fused(src[st], f0, dst[st], c->status, c->geo, ctx_tab<real>(c), coef, c->tx, c->ty, c->kp,
                         c->p.weno_mode == OLB_WENO_LEARNED ? c->mlp : nullptr, s);
 }
