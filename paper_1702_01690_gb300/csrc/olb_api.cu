@@ -293,22 +293,23 @@ static cudaError_t prepare_tile(olb_ctx *c)
                       : prepare_fused((float *)nullptr, c->tx, c->ty, c->kp, learned);
 }
 
-// Default shape: 16 x 8 nodes with 2 velocity lanes (FP64) or 32 x 16
-// nodes (FP32) when that still gives every SM two CTAs; otherwise 8 x 8
-// nodes with 4 (FP64, learned weights) or 8 (FP32) velocity lanes, so that
-// small grids (e.g. 1024 x 8) still put 8-16 warps on each busy SM (the
-// fastest shapes measured on a GB300).  Small grids take 7 x 8 tiles with 8
-// lanes instead when that lowers the most nodes any SM has to advance
-// (1024 x 8: 147 tiles of 56 nodes rather than 128 of 64 on 152 SMs).
-// olb_set_tile overrides.
+// Default shape, the fastest measured on a GB300 for each precision.  FP64:
+// 8 x 8 nodes with 4 velocity lanes (its faces of all 25 velocities fit in
+// shared memory, so a stage has one face pass and one barrier), except that
+// small grids take 7 x 8 tiles with 8 lanes when that lowers the most nodes
+// any SM has to advance (1024 x 8: 147 tiles of 56 nodes rather than 128 of
+// 64 on 152 SMs).  FP32: 32 x 16 nodes when that still gives every SM two
+// CTAs, otherwise 8 x 8 nodes with 8 lanes (4 with learned weights), so that
+// small grids still put 8-16 warps on each busy SM.  olb_set_tile overrides.
 static void default_tile(olb_ctx *c)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
     const bool learned = c->p.weno_mode == OLB_WENO_LEARNED;
-    const int big = is_fp64(c) ? 1 : 4;  // indices into TILE_*
-    const int small = is_fp64(c) || learned ? 0 : 5;
+    const bool fp64 = is_fp64(c);
+    const int big = fp64 ? 0 : 4;  // indices into TILE_*
+    const int small = fp64 || learned ? 0 : 5;
     const int narrow = 6;
     auto tiles = [&](int k) {
         return (long long)((c->geo.nx + TILE_X[k] - 1) / TILE_X[k]) * ((c->geo.ny + TILE_Y[k] - 1) / TILE_Y[k]);
@@ -316,7 +317,7 @@ static void default_tile(olb_ctx *c)
     auto most_nodes = [&](int k) { return (tiles(k) + sms - 1) / sms * TILE_X[k] * TILE_Y[k]; };
     int k = small;
     if (tiles(big) >= 2 * sms) k = big;
-    else if (!learned && most_nodes(narrow) < most_nodes(small)) k = narrow;
+    else if (fp64 && !learned && most_nodes(narrow) < most_nodes(small)) k = narrow;
     c->tx = TILE_X[k];
     c->ty = TILE_Y[k];
     c->kp = TILE_K[k];

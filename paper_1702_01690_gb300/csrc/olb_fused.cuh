@@ -68,8 +68,13 @@ struct FusedSmem {
     // inv_ds / n, E_q = (c/tau) n g_q(u_x, T) and g_q(u_y, T)
     static constexpr int L_DDX = 0, L_DDY = 1, L_LDX = 2, L_LDY = 3, L_DN = 4, L_E = 5, L_GY = 5 + NQ;
     real loc[KP > 1 ? 5 + 2 * NQ : 1][KP > 1 ? NN : 1];
-    real fx[KP][TY][TX + 1];
-    real fy[KP][TY + 1][TX];
+    // WENO-5 face values.  Small tiles (at most 64 nodes) hold the faces of
+    // all 25 velocities, so one pass computes them all and the node updates
+    // follow without further barriers; larger tiles hold KP velocities'.
+    static constexpr bool ALL_FACES = TX * TY <= 64;
+    static constexpr int KF = ALL_FACES ? NK : KP;
+    real fx[KF][TY][TX + 1];
+    real fy[KF][TY + 1][TX];
     real nw[2][TY];
 };
 
@@ -460,82 +465,110 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     const long long o = (long long)j * g.pitch + i;
     const real cf = cb - cit;
     const real cadv = cc * real(g.inv_ds);
-    for (int kb = 0; kb < NK; kb += KP) {
-        // faces of the KP velocities kb .. kb+KP-1, each computed once and
-        // enumerated densely: x faces of the tile rows unless xi_x = 0 (k1 = 2),
-        // then y faces of the tile columns unless xi_y = 0 (k2 = 2)
-        int end[KP], total = 0;
-#pragma unroll
-        for (int sub = 0; sub < KP; ++sub) {
-            const int k = kb + sub;
-            if (k < NK) total += (k / NQ != 2 ? nfx : 0) + (k % NQ != 2 ? nfy : 0);
-            end[sub] = total;
+    using Sf = FusedSmem<real, TX, TY, KP>;
+    constexpr int KF = Sf::KF;
+    // one face value: x face (r, c) or y face (r, c) of velocity k, stored in slot
+    auto face = [&](int k, int slot, bool along_x, int r, int c) {
+        const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
+        if (along_x) {
+            if (y0 + r < g.ny && x0 + c <= g.nx) {
+                // face at x = x0 + c: nodes x0+c-3 .. x0+c+2 are columns c+1 .. c+6
+                const real *row = &sm.pop[k][3 + r][0];
+                sm.fx[slot][r][c] =
+                    (k1 > 2) ? face_value<real, LEARNED>(mlp, row[c + 1], row[c + 2], row[c + 3], row[c + 4], row[c + 5])
+                             : face_value<real, LEARNED>(mlp, row[c + 6], row[c + 5], row[c + 4], row[c + 3], row[c + 2]);
+            }
+        } else if (x0 + c < g.nx && y0 + r <= g.ny) {
+            // face at y = y0 + r: rows y0+r-3 .. y0+r+2 are rows r .. r+5
+            const int cc4 = 4 + c;
+            const real(*P)[HX] = sm.pop[k];
+            sm.fy[slot][r][c] = (k2 > 2) ? face_value<real, LEARNED>(mlp, P[r][cc4], P[r + 1][cc4], P[r + 2][cc4],
+                                                                    P[r + 3][cc4], P[r + 4][cc4])
+                                        : face_value<real, LEARNED>(mlp, P[r + 5][cc4], P[r + 4][cc4], P[r + 3][cc4],
+                                                                    P[r + 2][cc4], P[r + 1][cc4]);
         }
-        __syncthreads();  // the previous velocities' faces are consumed
-        for (int e = tid; e < total; e += NT) {
-            int sub = 0, start = 0;
+    };
+    for (int kb = 0; kb < NK; kb += KF) {
+        __syncthreads();  // loc ready / the previous velocities' faces are consumed
+        if constexpr (Sf::ALL_FACES) {
+            // every face of every velocity once, enumerated densely: the x faces
+            // of the 20 velocities with xi_x != 0 (k1 != 2), then the y faces of
+            // the 20 with xi_y != 0 (k2 != 2)
+            for (int e = tid; e < 20 * (nfx + nfy); e += NT) {
+                if (e < 20 * nfx) {
+                    const int kx = e / nfx, f = e - kx * nfx;
+                    const int k = kx < 2 * NQ ? kx : kx + NQ;
+                    const int r = f / (TX + 1);
+                    face(k, k, true, r, f - r * (TX + 1));
+                } else {
+                    const int e2 = e - 20 * nfx, ky = e2 / nfy, f = e2 - ky * nfy, q = ky & 3;
+                    const int k = (ky >> 2) * NQ + (q < 2 ? q : q + 1);
+                    const int r = f / TX;
+                    face(k, k, false, r, f - r * TX);
+                }
+            }
+        } else {
+            // faces of the KP velocities kb .. kb+KP-1, each computed once and
+            // enumerated densely: x faces of the tile rows unless xi_x = 0
+            // (k1 = 2), then y faces of the tile columns unless xi_y = 0 (k2 = 2)
+            int end[KP], total = 0;
 #pragma unroll
-            for (int q = 0; q + 1 < KP; ++q)
-                if (e >= end[q]) {
-                    sub = q + 1;
-                    start = end[q];
-                }
-            const int k = kb + sub;
-            const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
-            int f = e - start;
-            if (k1 == 2) f += nfx;
-            if (f < nfx) {
-                const int r = f / (TX + 1), c = f - r * (TX + 1);
-                if (y0 + r < g.ny && x0 + c <= g.nx) {
-                    // face at x = x0 + c: nodes x0+c-3 .. x0+c+2 are columns c+1 .. c+6
-                    const real *row = &sm.pop[k][3 + r][0];
-                    sm.fx[sub][r][c] =
-                        (k1 > 2) ? face_value<real, LEARNED>(mlp, row[c + 1], row[c + 2], row[c + 3], row[c + 4], row[c + 5])
-                                 : face_value<real, LEARNED>(mlp, row[c + 6], row[c + 5], row[c + 4], row[c + 3], row[c + 2]);
-                }
-            } else {
-                const int e2 = f - nfx;
-                const int r = e2 / TX, c = e2 - r * TX;
-                if (x0 + c < g.nx && y0 + r <= g.ny) {
-                    // face at y = y0 + r: rows y0+r-3 .. y0+r+2 are rows r .. r+5
-                    const int cc4 = 4 + c;
-                    const real(*P)[HX] = sm.pop[k];
-                    sm.fy[sub][r][c] = (k2 > 2) ? face_value<real, LEARNED>(mlp, P[r][cc4], P[r + 1][cc4], P[r + 2][cc4],
-                                                                            P[r + 3][cc4], P[r + 4][cc4])
-                                                : face_value<real, LEARNED>(mlp, P[r + 5][cc4], P[r + 4][cc4],
-                                                                            P[r + 3][cc4], P[r + 2][cc4], P[r + 1][cc4]);
+            for (int sub = 0; sub < KP; ++sub) {
+                const int k = kb + sub;
+                if (k < NK) total += (k / NQ != 2 ? nfx : 0) + (k % NQ != 2 ? nfy : 0);
+                end[sub] = total;
+            }
+            for (int e = tid; e < total; e += NT) {
+                int sub = 0, start = 0;
+#pragma unroll
+                for (int q = 0; q + 1 < KP; ++q)
+                    if (e >= end[q]) {
+                        sub = q + 1;
+                        start = end[q];
+                    }
+                const int k = kb + sub;
+                int f = e - start;
+                if (k / NQ == 2) f += nfx;
+                if (f < nfx) {
+                    const int r = f / (TX + 1);
+                    face(k, sub, true, r, f - r * (TX + 1));
+                } else {
+                    const int r = (f - nfx) / TX;
+                    face(k, sub, false, r, f - nfx - r * TX);
                 }
             }
         }
         __syncthreads();
-        const int k = kb + lane_k;
-        if (active && k < NK) {
-            const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
-            const int r = ty + 3, c = tx + 4;
-            real dx = 0, dy = 0;
+        for (int ks = 0; ks < KF; ks += KP) {
+            const int slot = ks + lane_k;
+            const int k = kb + slot;
+            if (active && k < NK) {
+                const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
+                const int r = ty + 3, c = tx + 4;
+                real dx = 0, dy = 0;
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                dx = fma(t.D[k1][q], sm.pop[NQ * q + k2][r][c], dx);
-                dy = fma(t.D[k2][q], sm.pop[NQ * k1 + q][r][c], dy);
+                for (int q = 0; q < NQ; ++q) {
+                    dx = fma(t.D[k1][q], sm.pop[NQ * q + k2][r][c], dx);
+                    dy = fma(t.D[k2][q], sm.pop[NQ * k1 + q][r][c], dy);
+                }
+                const real f = sm.pop[k][r][c];
+                real Ek, gyk;
+                if constexpr (KP > 1) {
+                    Ek = sm.loc[Sf::L_E + k1][node];
+                    gyk = sm.loc[Sf::L_GY + k2][node];
+                } else {
+                    Ek = sel5(E, k1);
+                    gyk = sel5(gy, k2);
+                }
+                real adv = 0;
+                if (k1 != 2) adv = t.R[k1] * (sm.fx[slot][ty][tx + 1] - sm.fx[slot][ty][tx]);
+                if (k2 != 2) adv = fma(t.R[k2], sm.fy[slot][ty + 1][tx] - sm.fy[slot][ty][tx], adv);
+                // c L = -c xi.grad f - c F.grad_p f - (c/tau)(f - f^eq) with f^eq = n g g
+                // (Eqs. feq, g_alpha), combined with b f (and a f_n) as in Eq. rk3
+                real v = fma(cf, f, fma(Ek, gyk, -fma(Gx, dx, fma(Gy, dy, cadv * adv))));
+                if (ca != real(0)) v = fma(ca, fn[k * g.plane + o], v);
+                out[k * g.plane + o] = v;
             }
-            const real f = sm.pop[k][r][c];
-            real Ek, gyk;
-            if constexpr (KP > 1) {
-                using Sm = FusedSmem<real, TX, TY, KP>;
-                Ek = sm.loc[Sm::L_E + k1][node];
-                gyk = sm.loc[Sm::L_GY + k2][node];
-            } else {
-                Ek = sel5(E, k1);
-                gyk = sel5(gy, k2);
-            }
-            real adv = 0;
-            if (k1 != 2) adv = t.R[k1] * (sm.fx[lane_k][ty][tx + 1] - sm.fx[lane_k][ty][tx]);
-            if (k2 != 2) adv = fma(t.R[k2], sm.fy[lane_k][ty + 1][tx] - sm.fy[lane_k][ty][tx], adv);
-            // c L = -c xi.grad f - c F.grad_p f - (c/tau)(f - f^eq) with f^eq = n g g
-            // (Eqs. feq, g_alpha), combined with b f (and a f_n) as in Eq. rk3
-            real v = fma(cf, f, fma(Ek, gyk, -fma(Gx, dx, fma(Gy, dy, cadv * adv))));
-            if (ca != real(0)) v = fma(ca, fn[k * g.plane + o], v);
-            out[k * g.plane + o] = v;
         }
     }
 }
