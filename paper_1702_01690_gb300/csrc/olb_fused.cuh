@@ -66,16 +66,22 @@ struct FusedSmem {
     // per tile node, shared by the KP velocity lanes (with one lane they stay
     // in registers): the stencil sums of grad(Delta p) and grad(Laplacian n),
     // inv_ds / n, E_q = (c/tau) n g_q(u_x, T) and g_q(u_y, T)
-    static constexpr int L_DDX = 0, L_DDY = 1, L_LDX = 2, L_LDY = 3, L_DN = 4, L_E = 5, L_GY = 5 + NQ;
-    real loc[KP > 1 ? 5 + 2 * NQ : 1][KP > 1 ? NN : 1];
+    // (and, on tiles that keep every face, G_x = c F_x and G_y in L_G, L_G + 1)
+    static constexpr int L_DDX = 0, L_DDY = 1, L_LDX = 2, L_LDY = 3, L_DN = 4, L_E = 5, L_GY = 5 + NQ, L_G = 5 + 2 * NQ;
+    real loc[KP > 1 ? 7 + 2 * NQ : 1][KP > 1 ? NN : 1];
     // WENO-5 face values.  Small tiles (at most 64 nodes) hold the faces of
     // all 25 velocities, so one pass computes them all and the node updates
     // follow without further barriers; larger tiles hold KP velocities'.
     static constexpr bool ALL_FACES = TX * TY <= 64;
     static constexpr int KF = ALL_FACES ? NK : KP;
-    real fx[KF][TY][TX + 1];
+    union {
+        real fx[KF][TY][TX + 1];
+        // wall-face flux of each outgoing velocity (10) in each tile row, left
+        // and right diffuse wall: written and read between the moments and the
+        // force, before any face value is stored
+        real wflux[2][TY][10];
+    };
     real fy[KF][TY + 1][TX];
-    real nw[2][TY];
 };
 
 template <typename real>
@@ -172,10 +178,21 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     __syncthreads();
 
     // ---- 2. moments at every fluid position of the region that the 7 x 7
-    // force stencils reach (columns 1 .. HX-2)
+    // force stencils reach (columns 1 .. HX-2; ghost positions of walls and
+    // specular sides take the reflected fields in phase 3).  A tile at a
+    // diffuse wall also computes here, on warps of their own, the wall-face flux of every outgoing velocity in every tile
+    // row (Sec. 3.4.2: the WENO-5 face value at the wall from the three
+    // nearest fluid nodes and the two ghosts extrapolated from them) and
+    // stores those two ghosts; both need the phase-1 populations only, and
+    // the FP64 units of the sub-partitions with fewer moment warps have room.
     const f2 vdw_a = f2_of(g.a), vdw_b = f2_of(g.b);  // FP32 variant only
-    // (ghost positions of walls and specular sides take the reflected fields
-    // in phase 3)
+    const bool x_lo = g.walls && x0 == 0;                // ghost columns at x = 0
+    const bool x_hi = g.walls && (x0 + TX + 3 >= g.nx);  // ghost columns at x = nx ds
+    const bool left_wall = x_lo && g.wall_lo;
+    const bool right_wall = x_hi && g.wall_hi;
+    // wall-flux items start on the first warp after the moment positions
+    constexpr int e_flux = (HY * (HX - 2) + 31) / 32 * 32;
+    const int nflux = ((int)left_wall + (int)right_wall) * TY * 10;
     for (int e = tid; e < HY * (HX - 2); e += NT) {
         const int r = e / (HX - 2), c = e - r * (HX - 2) + 1;
         const int gx = x0 - 4 + c, gyr = y0 - 3 + r;
@@ -269,14 +286,34 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             }
         }
     }
+    // wall flux item f runs on thread (e_flux + f) mod NT: on the warps after
+    // those with moment positions
+    for (int f = (tid - e_flux % NT + NT) % NT; f < nflux; f += NT) {
+        // (wall, tile row tr, outgoing velocity v); the left wall's items first
+        const int side = (f >= TY * 10 || !left_wall) ? 1 : 0;
+        const int fr = f >= TY * 10 ? f - TY * 10 : f;
+        const int tr = fr / 10, v = fr - 10 * (fr / 10);
+        const int k1 = side ? 3 + v / 5 : v / 5;
+        const int k = NQ * k1 + v % 5;
+        // nearest three fluid nodes, nearest first; ghost layers 0 and 1
+        // are the next two columns outwards
+        const int c0 = side ? g.nx - 1 - (x0 - 4) : 0 - (x0 - 4);
+        const int dc = side ? -1 : 1;
+        const real a0 = sm.pop[k][tr + 3][c0], a1 = sm.pop[k][tr + 3][c0 + dc];
+        const real a2 = sm.pop[k][tr + 3][c0 + 2 * dc];
+        const real g0 = fma(real(3), a0 - a1, a2);
+        const real g1 = fma(real(6), a0, fma(real(-8), a1, real(3) * a2));
+        if (c0 - dc >= 0 && c0 - dc < HX) sm.pop[k][tr + 3][c0 - dc] = g0;
+        if (c0 - 2 * dc >= 0 && c0 - 2 * dc < HX) sm.pop[k][tr + 3][c0 - 2 * dc] = g1;
+        sm.wflux[side][tr][v] = t.R[k1] * face_value<real, LEARNED>(mlp, a2, a1, a0, g0, g1);
+    }
 
     // ---- 3. sides: n and Delta p reflected evenly into the ghost layers of
     // walls and specular planes (Sec. 3.4.3; y first, then x over every row,
-    // which makes the corners a double reflection), then the diffuse walls
-    const bool x_lo = g.walls && x0 == 0;                // ghost columns at x = 0
-    const bool x_hi = g.walls && (x0 + TX + 3 >= g.nx);  // ghost columns at x = nx ds
-    const bool left_wall = x_lo && g.wall_lo;
-    const bool right_wall = x_hi && g.wall_hi;
+    // which makes the corners a double reflection); at diffuse walls the
+    // incoming ghosts of the tile rows, f^eq_w = n_w g g (Sec. 3.4.2, Eq.
+    // diffuse_flux), with the wall density n_w of Eq. nw from the sum of the
+    // row's outgoing fluxes
     if (g.spec_y && (y0 == 0 || y0 + TY + 2 >= g.ny)) {
         __syncthreads();
         for (int e = tid; e < HY * HX; e += NT) {
@@ -291,79 +328,31 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     }
     if (x_lo || x_hi) {
         __syncthreads();
-        // mirror the fields; at diffuse walls extrapolate the outgoing populations
-        for (int e = tid; e < HY * HX; e += NT) {
-            const int r = e / HX, c = e - r * HX;
-            const int gx = x0 - 4 + c;
-            if (gx >= 0 && gx < g.nx) continue;
-            const bool right = gx >= g.nx;
-            const int m = right ? gx - g.nx : -1 - gx;  // ghost layer 0, 1, 2
-            if (m > 2) continue;
-            const int mirror = right ? 2 * g.nx - 1 - gx : -1 - gx;
-            const int cm = mirror - (x0 - 4);
-            sm.n[r][c] = sm.n[r][cm];
-            sm.dp[r][c] = sm.dp[r][cm];
-            if (m > 1 || !(right ? g.wall_hi : g.wall_lo)) continue;
-            // nearest three fluid nodes, nearest first
-            const int c0 = right ? g.nx - 1 - (x0 - 4) : 0 - (x0 - 4);
-            const int dc = right ? -1 : 1;
+        constexpr int e_in = (HY * HX + 31) / 32 * 32;  // first incoming-ghost item, on a warp boundary
+        const int nin = ((int)left_wall + (int)right_wall) * TY * 30;
+        for (int e = tid; e < e_in + nin; e += NT) {
+            if (e < HY * HX) {
+                const int r = e / HX, c = e - r * HX;
+                const int gx = x0 - 4 + c;
+                if (gx >= 0 && gx < g.nx) continue;
+                const bool right = gx >= g.nx;
+                if ((right ? gx - g.nx : -1 - gx) > 2) continue;  // beyond ghost layer 2
+                const int cm = (right ? 2 * g.nx - 1 - gx : -1 - gx) - (x0 - 4);
+                sm.n[r][c] = sm.n[r][cm];
+                sm.dp[r][c] = sm.dp[r][cm];
+            } else if (e >= e_in) {
+                // (wall, tile row tr, ghost layer m, incoming velocity v)
+                const int f = e - e_in;
+                const int side = (f >= TY * 30 || !left_wall) ? 1 : 0;
+                const int fr = f >= TY * 30 ? f - TY * 30 : f;
+                const int tr = fr / 30, m = (fr - 30 * tr) / 10, v = fr - 30 * tr - 10 * m;
+                const int c = side ? g.nx + m - (x0 - 4) : -1 - m - (x0 - 4);
+                if (c < 0 || c >= HX) continue;
+                real flux = sm.wflux[side][tr][0];
 #pragma unroll
-            for (int k1 = 0; k1 < NQ; ++k1) {
-                const bool out_going = right ? (k1 > 2) : (k1 < 2);
-                if (!out_going) continue;
-#pragma unroll
-                for (int k2 = 0; k2 < NQ; ++k2) {
-                    const int k = NQ * k1 + k2;
-                    const real a0 = sm.pop[k][r][c0], a1 = sm.pop[k][r][c0 + dc], a2 = sm.pop[k][r][c0 + 2 * dc];
-                    sm.pop[k][r][c] = m == 0 ? fma(real(3), a0 - a1, a2)
-                                             : fma(real(6), a0, fma(real(-8), a1, real(3) * a2));
-                }
-            }
-        }
-    }
-    if (left_wall || right_wall) {
-        // wall densities of the tile rows: one warp per (wall, row), lanes
-        // 0..9 take the outgoing velocities, the wall-face flux with inline
-        // extrapolated ghosts, reduced by shuffles
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int w = warp; w < 2 * TY; w += NT / 32) {
-            const int side = w / TY, tr = w - side * TY;
-            if ((side == 0 && !left_wall) || (side == 1 && !right_wall)) continue;
-            real flux = real(0);
-            if (lane < 10) {
-                const int k1 = side ? 3 + lane / 5 : lane / 5;
-                const int k = NQ * k1 + lane % 5;
-                const int c0 = side ? g.nx - 1 - (x0 - 4) : 0 - (x0 - 4);
-                const int dc = side ? -1 : 1;
-                const real a0 = sm.pop[k][tr + 3][c0], a1 = sm.pop[k][tr + 3][c0 + dc];
-                const real a2 = sm.pop[k][tr + 3][c0 + 2 * dc];
-                const real g0 = fma(real(3), a0 - a1, a2);
-                const real g1 = fma(real(6), a0, fma(real(-8), a1, real(3) * a2));
-                flux = t.R[k1] * face_value<real, LEARNED>(mlp, a2, a1, a0, g0, g1);
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) flux += __shfl_xor_sync(0xffffffffu, flux, off);
-            if (lane == 0) sm.nw[side][tr] = -flux * t.inv_den[side];
-        }
-        __syncthreads();
-        // incoming ghosts (3 layers) in the tile rows: f^eq_w = n_w g g
-        for (int e = tid; e < TY * HX; e += NT) {
-            const int tr = e / HX, c = e - tr * HX;
-            const int gx = x0 - 4 + c;
-            if (gx >= 0 && gx < g.nx) continue;
-            const bool right = gx >= g.nx;
-            const int m = right ? gx - g.nx : -1 - gx;
-            if (m > 2 || !(right ? right_wall : left_wall)) continue;
-            const real nwv = sm.nw[right ? 1 : 0][tr];
-#pragma unroll
-            for (int k1 = 0; k1 < NQ; ++k1) {
-                const bool in_coming = right ? (k1 < 2) : (k1 > 2);
-                if (!in_coming) continue;
-#pragma unroll
-                for (int k2 = 0; k2 < NQ; ++k2) {
-                    const int k = NQ * k1 + k2;
-                    sm.pop[k][tr + 3][c] = nwv * t.geqw[right ? 1 : 0][k];
-                }
+                for (int q = 1; q < 10; ++q) flux += sm.wflux[side][tr][q];
+                const int k = NQ * (side ? v / 5 : 3 + v / 5) + v % 5;
+                sm.pop[k][tr + 3][c] = (-flux * t.inv_den[side]) * t.geqw[side][k];
             }
         }
     }
@@ -453,16 +442,22 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             }
         }
         __syncthreads();
-        if (active) {
+        // G = c F at the node: in registers of each lane, or, on tiles that
+        // keep every face, once per node in shared memory (read after the
+        // barrier that ends the face pass)
+        if (active && (!Sm::ALL_FACES || lane_k == 0)) {
             const real dn = sm.loc[Sm::L_DN][node];
             Gx = cc * fma(sm.loc[Sm::L_DDX][node], dn, sg3 * sm.loc[Sm::L_LDX][node]);
             Gy = cc * fma(sm.loc[Sm::L_DDY][node], dn, sg3 * sm.loc[Sm::L_LDY][node]);
+            if constexpr (Sm::ALL_FACES) {
+                sm.loc[Sm::L_G][node] = Gx;
+                sm.loc[Sm::L_G + 1][node] = Gy;
+            }
         }
     }
 
     // ---- 5. advection, collision and RK combination, KP velocities at a time
     const int nfx = (TX + 1) * TY, nfy = TX * (TY + 1);
-    const long long o = (long long)j * g.pitch + i;
     const real cf = cb - cit;
     const real cadv = cc * real(g.inv_ds);
     using Sf = FusedSmem<real, TX, TY, KP>;
@@ -487,6 +482,27 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                                         : face_value<real, LEARNED>(mlp, P[r + 5][cc4], P[r + 4][cc4], P[r + 3][cc4],
                                                                     P[r + 2][cc4], P[r + 1][cc4]);
         }
+    };
+    // node update of velocity k (faces in slot) at tile node (tx_, ty_)
+    auto update = [&](int k, int slot, int tx_, int ty_, real Gx_, real Gy_, real Ek, real gyk) {
+        const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
+        const int r = ty_ + 3, c = tx_ + 4;
+        real dx = 0, dy = 0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            dx = fma(t.D[k1][q], sm.pop[NQ * q + k2][r][c], dx);
+            dy = fma(t.D[k2][q], sm.pop[NQ * k1 + q][r][c], dy);
+        }
+        const real f = sm.pop[k][r][c];
+        real adv = 0;
+        if (k1 != 2) adv = t.R[k1] * (sm.fx[slot][ty_][tx_ + 1] - sm.fx[slot][ty_][tx_]);
+        if (k2 != 2) adv = fma(t.R[k2], sm.fy[slot][ty_ + 1][tx_] - sm.fy[slot][ty_][tx_], adv);
+        // c L = -c xi.grad f - c F.grad_p f - (c/tau)(f - f^eq) with f^eq = n g g
+        // (Eqs. feq, g_alpha), combined with b f (and a f_n) as in Eq. rk3
+        real v = fma(cf, f, fma(Ek, gyk, -fma(Gx_, dx, fma(Gy_, dy, cadv * adv))));
+        const long long o = (long long)(y0 + ty_) * g.pitch + (x0 + tx_);
+        if (ca != real(0)) v = fma(ca, fn[k * g.plane + o], v);
+        out[k * g.plane + o] = v;
     };
     for (int kb = 0; kb < NK; kb += KF) {
         __syncthreads();  // loc ready / the previous velocities' faces are consumed
@@ -539,19 +555,20 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             }
         }
         __syncthreads();
-        for (int ks = 0; ks < KF; ks += KP) {
-            const int slot = ks + lane_k;
-            const int k = kb + slot;
+        if constexpr (Sf::ALL_FACES) {
+            // node updates, enumerated densely over (velocity, tile node)
+            for (int e = tid; e < NK * NN; e += NT) {
+                const int k = e / NN, nd = e - k * NN;
+                const int tx_ = nd % TX, ty_ = nd / TX;
+                if (x0 + tx_ >= g.nx || y0 + ty_ >= g.ny) continue;
+                const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
+                update(k, k, tx_, ty_, sm.loc[Sf::L_G][nd], sm.loc[Sf::L_G + 1][nd], sm.loc[Sf::L_E + k1][nd],
+                       sm.loc[Sf::L_GY + k2][nd]);
+            }
+        } else {
+            const int k = kb + lane_k;
             if (active && k < NK) {
                 const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
-                const int r = ty + 3, c = tx + 4;
-                real dx = 0, dy = 0;
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    dx = fma(t.D[k1][q], sm.pop[NQ * q + k2][r][c], dx);
-                    dy = fma(t.D[k2][q], sm.pop[NQ * k1 + q][r][c], dy);
-                }
-                const real f = sm.pop[k][r][c];
                 real Ek, gyk;
                 if constexpr (KP > 1) {
                     Ek = sm.loc[Sf::L_E + k1][node];
@@ -560,14 +577,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                     Ek = sel5(E, k1);
                     gyk = sel5(gy, k2);
                 }
-                real adv = 0;
-                if (k1 != 2) adv = t.R[k1] * (sm.fx[slot][ty][tx + 1] - sm.fx[slot][ty][tx]);
-                if (k2 != 2) adv = fma(t.R[k2], sm.fy[slot][ty + 1][tx] - sm.fy[slot][ty][tx], adv);
-                // c L = -c xi.grad f - c F.grad_p f - (c/tau)(f - f^eq) with f^eq = n g g
-                // (Eqs. feq, g_alpha), combined with b f (and a f_n) as in Eq. rk3
-                real v = fma(cf, f, fma(Ek, gyk, -fma(Gx, dx, fma(Gy, dy, cadv * adv))));
-                if (ca != real(0)) v = fma(ca, fn[k * g.plane + o], v);
-                out[k * g.plane + o] = v;
+                update(k, lane_k, tx, ty, Gx, Gy, Ek, gyk);
             }
         }
     }
@@ -586,9 +596,24 @@ constexpr size_t fused_smem_bytes()
     return LEARNED ? mlp_offset<real, TX, TY, KP>() + (MLP_P + 1) * sizeof(float) : sizeof(FusedSmem<real, TX, TY, KP>);
 }
 
+// CTAs per SM that the register allocation must leave room for: as many as
+// the shared memory (228 KB per SM, 1 KB of it reserved per CTA) and the
+// 2048 threads of an SM allow.  Without this bound the compiler may take
+// more registers than that occupancy leaves (e.g. 80 for a 512-thread CTA
+// that could otherwise share its SM).  Learned-weight instances keep the
+// registers their network needs.
+constexpr int fused_min_ctas(size_t smem_bytes, int threads, bool learned = false)
+{
+    const int by_smem = (int)((228 * 1024) / (smem_bytes + 1024)), by_threads = 2048 / threads;
+    const int n = by_smem < by_threads ? by_smem : by_threads;
+    return learned || n < 1 ? 1 : n;
+}
+
 // Single grid: one CTA per tile.
 template <typename real, int TX, int TY, int KP, bool LEARNED>
-__global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT)
+__global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT,
+                                  fused_min_ctas(fused_smem_bytes<real, TX, TY, KP, LEARNED>(),
+                                                 FusedSmem<real, TX, TY, KP>::NT, LEARNED))
 k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
         const __grid_constant__ Geo g, const __grid_constant__ Tab<real> t, real ca, real cb, real cc,
         const float *__restrict__ mlp)
@@ -624,7 +649,10 @@ static_assert(sizeof(BatchRun<double>) % 16 == 0, "BatchRun<double> must be a wh
 static_assert(sizeof(BatchRun<float>) % 16 == 0, "BatchRun<float> must be a whole number of int4 words");
 
 template <typename real, int TX, int TY, int KP>
-__global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT)
+__global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT,
+                                  // at most two: more would spill the per-item state
+                                  fused_min_ctas(sizeof(FusedSmem<real, TX, TY, KP>) + sizeof(BatchRun<real>),
+                                                 FusedSmem<real, TX, TY, KP>::NT) > 1 ? 2 : 1)
 k_fused_batch(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
               const BatchRun<real> *__restrict__ runs, const int *__restrict__ tile_start, int nruns, int total,
               real ca, real cb, real ccoef)
