@@ -506,7 +506,38 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     };
     for (int kb = 0; kb < NK; kb += KF) {
         __syncthreads();  // loc ready / the previous velocities' faces are consumed
-        if constexpr (Sf::ALL_FACES) {
+        if constexpr (Sf::ALL_FACES && !LEARNED && sizeof(real) == 4) {
+            // FP32 (issue-bound): every face of every velocity once, in strips
+            // of SX (SY) consecutive faces along a tile row (column), each
+            // strip in the upwind direction of its velocity: the x strips of
+            // the 20 velocities with xi_x != 0 (k1 != 2), then the y strips of
+            // the 20 with xi_y != 0 (k2 != 2).  (In FP64 the FP64 unit paces
+            // each warp, and the fewer, longer strip items leave too few warps
+            // per sub-partition at the end of the pass: single faces are faster.)
+            constexpr int SX = (TX + 1) % 4 == 0 ? 4 : ((TX + 1) % 3 == 0 ? 3 : 1);
+            constexpr int SY = (TY + 1) % 4 == 0 ? 4 : ((TY + 1) % 3 == 0 ? 3 : 1);
+            constexpr int NSX = (TX + 1) / SX, NSY = (TY + 1) / SY;    // strips per row, per column
+            constexpr int nsx = NSX * TY, nsy = NSY * TX;              // strips per velocity
+            for (int e = tid; e < 20 * (nsx + nsy); e += NT) {
+                if (e < 20 * nsx) {
+                    const int kx = e / nsx, f = e - kx * nsx;
+                    const int k = kx < 2 * NQ ? kx : kx + NQ;
+                    const int r = f / NSX, cs = (f - r * NSX) * SX;
+                    // face at x = x0 + c reads columns c+1 .. c+5 (xi_x > 0) or c+6 .. c+2
+                    const real *row = &sm.pop[k][3 + r][0];
+                    if (k / NQ > 2) weno5_strip<SX>(row + cs + 1, 1, &sm.fx[k][r][cs], 1);
+                    else weno5_strip<SX>(row + cs + SX + 5, -1, &sm.fx[k][r][cs + SX - 1], -1);
+                } else {
+                    const int e2 = e - 20 * nsx, ky = e2 / nsy, f = e2 - ky * nsy, q = ky & 3;
+                    const int k = (ky >> 2) * NQ + (q < 2 ? q : q + 1);
+                    const int rs = (f / TX) * SY, c = f - (f / TX) * TX;
+                    // face at y = y0 + r reads rows r .. r+4 (xi_y > 0) or r+5 .. r+1
+                    if (k % NQ > 2) weno5_strip<SY>(&sm.pop[k][rs][4 + c], HX, &sm.fy[k][rs][c], TX);
+                    else weno5_strip<SY>(&sm.pop[k][rs + SY + 4][4 + c], -HX, &sm.fy[k][rs + SY - 1][c], -TX);
+                }
+            }
+            // (faces outside the grid are computed from staged values and never read)
+        } else if constexpr (Sf::ALL_FACES) {
             // every face of every velocity once, enumerated densely: the x faces
             // of the 20 velocities with xi_x != 0 (k1 != 2), then the y faces of
             // the 20 with xi_y != 0 (k2 != 2)

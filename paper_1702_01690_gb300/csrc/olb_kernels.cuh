@@ -76,13 +76,17 @@ __device__ __forceinline__ double recip_nr(double d)
 // two or three vanish; those cases take Table tab:weno (the ideal weights of
 // the vanishing set).  If the products underflow without an exact zero the
 // min-scaled form delta_q (s/sigma_q)^2 is used instead.
-__device__ __forceinline__ double weno5(double v0, double v1, double v2, double v3, double v4)
+//
+// weno5_core takes the first differences, the squares q12 = d12^2, q23 =
+// d23^2 and h12 = 2.5 q12, h23 = 2.5 q23; weno5 (one face) and weno5_strip
+// (consecutive faces, carrying those values from face to face) both end in
+// it, with the same operations on the same operands, so they agree bit for bit.
+__device__ __forceinline__ double weno5_core(double d01, double d12, double d23, double d34, double q12, double q23,
+                                             double h12, double h23, double v2)
 {
-    const double d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
-    const double q12 = d12 * d12, q23 = d23 * d23;
-    const double s1 = fma(d01, fma(-2.75, d12, d01), 2.5 * q12);
+    const double s1 = fma(d01, fma(-2.75, d12, d01), h12);
     const double s2 = fma(-1.25 * d12, d23, q12 + q23);
-    const double s3 = fma(d34, fma(-2.75, d23, d34), 2.5 * q23);
+    const double s3 = fma(d34, fma(-2.75, d23, d34), h23);
     const double G1 = fma(5.0, d12, -2.0 * d01);
     const double G2 = fma(2.0, d23, d12);
     const double G3 = fma(4.0, d23, -d34);
@@ -110,18 +114,23 @@ __device__ __forceinline__ double weno5(double v0, double v1, double v2, double 
     }
     return fma(fma(A1, G1, fma(A2, G2, A3 * G3)), recip_nr(6.0 * den), v2);
 }
+__device__ __forceinline__ double weno5(double v0, double v1, double v2, double v3, double v4)
+{
+    const double d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
+    const double q12 = d12 * d12, q23 = d23 * d23;
+    return weno5_core(d01, d12, d23, d34, q12, q23, 2.5 * q12, 2.5 * q23, v2);
+}
 
 // FP32 form (same forms and candidates): the products of four squared
 // indicators underflow in single precision, so the weights are always the
 // min-scaled 10 delta_q (s/sigma_q)^2 (same normalised weights), with Table
 // tab:weno when an indicator vanishes.
-__device__ __forceinline__ float weno5(float v0, float v1, float v2, float v3, float v4)
+__device__ __forceinline__ float weno5_core(float d01, float d12, float d23, float d34, float q12, float q23, float h12,
+                                            float h23, float v2)
 {
-    const float d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
-    const float q12 = d12 * d12, q23 = d23 * d23;
-    const float s1 = fmaf(d01, fmaf(-2.75f, d12, d01), 2.5f * q12);
+    const float s1 = fmaf(d01, fmaf(-2.75f, d12, d01), h12);
     const float s2 = fmaf(-1.25f * d12, d23, q12 + q23);
-    const float s3 = fmaf(d34, fmaf(-2.75f, d23, d34), 2.5f * q23);
+    const float s3 = fmaf(d34, fmaf(-2.75f, d23, d34), h23);
     const float G1 = fmaf(5.0f, d12, -2.0f * d01);
     const float G2 = fmaf(2.0f, d23, d12);
     const float G3 = fmaf(4.0f, d23, -d34);
@@ -138,6 +147,40 @@ __device__ __forceinline__ float weno5(float v0, float v1, float v2, float v3, f
         w3 = (s3 == 0.0f) ? 3.0f : 0.0f;
     }
     return fmaf(fmaf(w1, G1, fmaf(w2, G2, w3 * G3)), __fdividef(1.0f, 6.0f * (w1 + w2 + w3)), v2);
+}
+__device__ __forceinline__ float weno5(float v0, float v1, float v2, float v3, float v4)
+{
+    const float d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
+    const float q12 = d12 * d12, q23 = d23 * d23;
+    return weno5_core(d01, d12, d23, d34, q12, q23, 2.5f * q12, 2.5f * q23, v2);
+}
+
+// S consecutive faces along a row or column, in the upwind direction: the
+// stencil v_0 .. v_4 of face j is p[(j + m) step], m = 0..4, and its value
+// goes to out[j ostep].  Neighbouring faces share three first differences,
+// two squares and one scaled square, which are carried instead of recomputed
+// (5 fewer operations per face after the first).
+template <int S, typename real>
+__device__ __forceinline__ void weno5_strip(const real *p, int step, real *out, int ostep)
+{
+    real v2 = p[2 * step], v3 = p[3 * step];
+    const real v1 = p[step];
+    real d01 = v1 - p[0], d12 = v2 - v1, d23 = v3 - v2;
+    real q12 = d12 * d12, h12 = real(2.5) * q12;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        const real v4 = p[(j + 4) * step];
+        const real d34 = v4 - v3;
+        const real q23 = d23 * d23, h23 = real(2.5) * q23;
+        out[j * ostep] = weno5_core(d01, d12, d23, d34, q12, q23, h12, h23, v2);
+        d01 = d12;
+        d12 = d23;
+        d23 = d34;
+        q12 = q23;
+        h12 = h23;
+        v2 = v3;
+        v3 = v4;
+    }
 }
 
 // ---------------------------------------------------------------- helpers

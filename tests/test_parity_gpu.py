@@ -364,6 +364,27 @@ def test_every_tile_shape_gives_identical_results(olb, side_x):
     assert np.array_equal(ctx.get_populations(), ref)
 
 
+@pytest.mark.parametrize("side_x", [0, 1])
+def test_every_tile_shape_gives_identical_results_fp32(olb, side_x):
+    """FP32 + Kahan: the small tiles compute their faces in strips that carry
+    differences and squares from face to face, the large tiles one face at a
+    time; the arithmetic is the same, so every shape agrees bit for bit."""
+    p = inputs.RunParams(nx=45, ny=19, ds=1.0 / 45, dt=0.2 / 45 / inputs.P_MAX, tau=0.01,
+                         Tw=(0.85, 0.95), side_x=side_x)
+    fl = noisy(p, seed=9, amp=0.05, uamp=0.01)
+    ref = None
+    for shape in ((32, 16, 1), (8, 8, 4), (16, 8, 2), (16, 8, 1), (32, 8, 1), (8, 8, 8), (7, 8, 8)):
+        ctx = olb.create(p, olb.FP32_KAHAN)
+        ctx.set_tile(*shape)
+        ctx.init_fields(*fl)
+        assert ctx.step(4) == 0
+        f = ctx.get_populations()
+        if ref is None:
+            ref = f
+        else:
+            assert np.array_equal(f, ref), shape
+
+
 def test_fp32_kahan_fine_grid_laplace(olb):
     """FP32 + Kahan against the FP64 path on the Laplace drop at 1024^2 (fine
     grid, where the capillary stencil cancels to O(ds^3) of its terms): n, T
