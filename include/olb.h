@@ -195,7 +195,10 @@ int olb_profile(olb_ctx *ctx, int nsteps, double *ms, int *launches);
  * at once (kp lanes of tx*ty threads, each rounded up to whole warps).
  * Compiled shapes (tx, ty, kp): (8,8,4), (16,8,2), (16,8,1), (32,8,1),
  * (32,16,1), (8,8,8), (7,8,8); olb_create picks one from the
- * grid size.  With OLB_WENO_LEARNED only (8,8,4), (16,8,2), (32,16,1).  olb_set_tile returns
+ * grid size (FP64: (8,8,4), or (7,8,8) when that lowers the most nodes one
+ * SM advances; FP32: (32,16,1) on grids with at least two of its tiles per
+ * SM, else (8,8,8), or (8,8,4) with learned weights).  With
+ * OLB_WENO_LEARNED only (8,8,4), (16,8,2), (32,16,1).  olb_set_tile returns
  * OLB_ERR_ARG for any other shape; results do not depend on the shape.
  * Not part of the paper (a tuning knob). */
 int olb_set_tile(olb_ctx *ctx, int tx, int ty, int kp);
