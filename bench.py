@@ -58,7 +58,7 @@ VALUES_PER_NODE_STEP = 200
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per stage launch, averaged over the three stages of
 # a step, from one ncu capture of exactly this kernel build on this workload
-# (stage 1: 1.72 MB, stages 2 and 3: 3.36 MB each; writes still in L2).  Any
+# (stage 1: 1.71 MB, stages 2 and 3: 3.35 MB each; writes still in L2).  Any
 # other kernel or workload reports null.
 DRAM_TRAFFIC_PER_LAUNCH = {("planar", None, "k_fused<double,7,8,8>"): 2.81e6}
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12

@@ -61,7 +61,7 @@ __device__ __forceinline__ double recip_nr(double d)
 // indicators of Eq. weno5_sigma (13/12 a_q^2 + 1/4 b_q^2, a_q and b_q linear
 // in two neighbouring differences) are positive-definite quadratic forms:
 //   12 sigma_1 / 16 = d01^2 - 11/4 d01 d12 + 5/2 d12^2
-//   12 sigma_2 / 16 = d12^2 + d23^2 - 5/4 d12 d23
+//   12 sigma_2 / 16 = d12^2 + d23^2 - 5/4 d12 d23 = d12 (d12 - 5/4 d23) + d23^2
 //   12 sigma_3 / 16 = d34^2 - 11/4 d23 d34 + 5/2 d23^2
 // (the weights only depend on ratios of the sigma_q, so the common factor
 // 12/16 is dropped), and 6 (Fhat^q - v2) of Eq. weno5_flux are
@@ -77,15 +77,15 @@ __device__ __forceinline__ double recip_nr(double d)
 // the vanishing set).  If the products underflow without an exact zero the
 // min-scaled form delta_q (s/sigma_q)^2 is used instead.
 //
-// weno5_core takes the first differences, the squares q12 = d12^2, q23 =
-// d23^2 and h12 = 2.5 q12, h23 = 2.5 q23; weno5 (one face) and weno5_strip
+// weno5_core takes the first differences, q23 = d23^2 and h12 = 2.5 d12^2,
+// h23 = 2.5 d23^2; weno5 (one face) and weno5_strip
 // (consecutive faces, carrying those values from face to face) both end in
 // it, with the same operations on the same operands, so they agree bit for bit.
-__device__ __forceinline__ double weno5_core(double d01, double d12, double d23, double d34, double q12, double q23,
-                                             double h12, double h23, double v2)
+__device__ __forceinline__ double weno5_core(double d01, double d12, double d23, double d34, double q23, double h12,
+                                             double h23, double v2)
 {
     const double s1 = fma(d01, fma(-2.75, d12, d01), h12);
-    const double s2 = fma(-1.25 * d12, d23, q12 + q23);
+    const double s2 = fma(d12, fma(-1.25, d23, d12), q23);
     const double s3 = fma(d34, fma(-2.75, d23, d34), h23);
     const double G1 = fma(5.0, d12, -2.0 * d01);
     const double G2 = fma(2.0, d23, d12);
@@ -118,18 +118,18 @@ __device__ __forceinline__ double weno5(double v0, double v1, double v2, double 
 {
     const double d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
     const double q12 = d12 * d12, q23 = d23 * d23;
-    return weno5_core(d01, d12, d23, d34, q12, q23, 2.5 * q12, 2.5 * q23, v2);
+    return weno5_core(d01, d12, d23, d34, q23, 2.5 * q12, 2.5 * q23, v2);
 }
 
 // FP32 form (same forms and candidates): the products of four squared
 // indicators underflow in single precision, so the weights are always the
 // min-scaled 10 delta_q (s/sigma_q)^2 (same normalised weights), with Table
 // tab:weno when an indicator vanishes.
-__device__ __forceinline__ float weno5_core(float d01, float d12, float d23, float d34, float q12, float q23, float h12,
-                                            float h23, float v2)
+__device__ __forceinline__ float weno5_core(float d01, float d12, float d23, float d34, float q23, float h12, float h23,
+                                            float v2)
 {
     const float s1 = fmaf(d01, fmaf(-2.75f, d12, d01), h12);
-    const float s2 = fmaf(-1.25f * d12, d23, q12 + q23);
+    const float s2 = fmaf(d12, fmaf(-1.25f, d23, d12), q23);
     const float s3 = fmaf(d34, fmaf(-2.75f, d23, d34), h23);
     const float G1 = fmaf(5.0f, d12, -2.0f * d01);
     const float G2 = fmaf(2.0f, d23, d12);
@@ -152,31 +152,30 @@ __device__ __forceinline__ float weno5(float v0, float v1, float v2, float v3, f
 {
     const float d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
     const float q12 = d12 * d12, q23 = d23 * d23;
-    return weno5_core(d01, d12, d23, d34, q12, q23, 2.5f * q12, 2.5f * q23, v2);
+    return weno5_core(d01, d12, d23, d34, q23, 2.5f * q12, 2.5f * q23, v2);
 }
 
 // S consecutive faces along a row or column, in the upwind direction: the
 // stencil v_0 .. v_4 of face j is p[(j + m) step], m = 0..4, and its value
-// goes to out[j ostep].  Neighbouring faces share three first differences,
-// two squares and one scaled square, which are carried instead of recomputed
-// (5 fewer operations per face after the first).
+// goes to out[j ostep].  Neighbouring faces share three first differences
+// and one scaled square, which are carried instead of recomputed (4 fewer
+// operations per face after the first).
 template <int S, typename real>
 __device__ __forceinline__ void weno5_strip(const real *p, int step, real *out, int ostep)
 {
     real v2 = p[2 * step], v3 = p[3 * step];
     const real v1 = p[step];
     real d01 = v1 - p[0], d12 = v2 - v1, d23 = v3 - v2;
-    real q12 = d12 * d12, h12 = real(2.5) * q12;
+    real h12 = real(2.5) * (d12 * d12);
 #pragma unroll
     for (int j = 0; j < S; ++j) {
         const real v4 = p[(j + 4) * step];
         const real d34 = v4 - v3;
         const real q23 = d23 * d23, h23 = real(2.5) * q23;
-        out[j * ostep] = weno5_core(d01, d12, d23, d34, q12, q23, h12, h23, v2);
+        out[j * ostep] = weno5_core(d01, d12, d23, d34, q23, h12, h23, v2);
         d01 = d12;
         d12 = d23;
         d23 = d34;
-        q12 = q23;
         h12 = h23;
         v2 = v3;
         v3 = v4;
