@@ -180,11 +180,12 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     // ---- 2. moments at every fluid position of the region that the 7 x 7
     // force stencils reach (columns 1 .. HX-2; ghost positions of walls and
     // specular sides take the reflected fields in phase 3).  A tile at a
-    // diffuse wall also computes here, on warps of their own, the wall-face flux of every outgoing velocity in every tile
-    // row (Sec. 3.4.2: the WENO-5 face value at the wall from the three
-    // nearest fluid nodes and the two ghosts extrapolated from them) and
-    // stores those two ghosts; both need the phase-1 populations only, and
-    // the FP64 units of the sub-partitions with fewer moment warps have room.
+    // diffuse wall also computes here, on warps of their own, the wall-face
+    // flux of every outgoing velocity in every tile row (Sec. 3.4.2: the
+    // WENO-5 face value at the wall from the three nearest fluid nodes and the
+    // two ghosts extrapolated from them) and stores those two ghosts; both
+    // need the phase-1 populations only, and the FP64 units of the
+    // sub-partitions with fewer moment warps have room.
     const f2 vdw_a = f2_of(g.a), vdw_b = f2_of(g.b);  // FP32 variant only
     const bool x_lo = g.walls && x0 == 0;                // ghost columns at x = 0
     const bool x_hi = g.walls && (x0 + TX + 3 >= g.nx);  // ghost columns at x = nx ds
