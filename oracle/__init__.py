@@ -79,42 +79,65 @@ class OrcParams(ctypes.Structure):
 _D = ctypes.POINTER(ctypes.c_double)
 
 
+def _declare(L):
+    """Argument and result types of the oracle's exported calls."""
+    L.orc_hermite.restype = ctypes.c_double
+    L.orc_hermite.argtypes = [ctypes.c_int, ctypes.c_double]
+    L.orc_quadrature.argtypes = [_D, _D]
+    L.orc_g.restype = ctypes.c_double
+    L.orc_g.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.orc_feq.argtypes = [ctypes.c_double] * 4 + [_D]
+    L.orc_dp_line.argtypes = [_D, _D]
+    L.orc_moments_node.argtypes = [_D, _D]
+    L.orc_pw.restype = ctypes.c_double
+    L.orc_pw.argtypes = [ctypes.c_double] * 4
+    L.orc_grad_stencil.argtypes = [_D]
+    L.orc_glap_stencil.argtypes = [_D]
+    L.orc_weno5.restype = ctypes.c_double
+    L.orc_weno5.argtypes = [_D, _D]
+    L.orc_create.restype = ctypes.c_void_p
+    L.orc_create.argtypes = [ctypes.POINTER(OrcParams)]
+    L.orc_destroy.argtypes = [ctypes.c_void_p]
+    L.orc_init.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
+    L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.orc_get_f.argtypes = [ctypes.c_void_p, _D]
+    L.orc_set_f.argtypes = [ctypes.c_void_p, _D]
+    L.orc_get_moments.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
+    L.orc_eval.argtypes = [ctypes.c_void_p, _D, _D, _D]
+    L.orc_weno5_learned.restype = ctypes.c_double
+    L.orc_weno5_learned.argtypes = [_D, _D, _D]
+    L.orc_set_mlp.argtypes = [ctypes.c_void_p, _D]
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_max_threads.restype = ctypes.c_int
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
-            L = ctypes.CDLL(path)
-            L.orc_hermite.restype = ctypes.c_double
-            L.orc_hermite.argtypes = [ctypes.c_int, ctypes.c_double]
-            L.orc_quadrature.argtypes = [_D, _D]
-            L.orc_g.restype = ctypes.c_double
-            L.orc_g.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
-            L.orc_feq.argtypes = [ctypes.c_double] * 4 + [_D]
-            L.orc_dp_line.argtypes = [_D, _D]
-            L.orc_moments_node.argtypes = [_D, _D]
-            L.orc_pw.restype = ctypes.c_double
-            L.orc_pw.argtypes = [ctypes.c_double] * 4
-            L.orc_grad_stencil.argtypes = [_D]
-            L.orc_glap_stencil.argtypes = [_D]
-            L.orc_weno5.restype = ctypes.c_double
-            L.orc_weno5.argtypes = [_D, _D]
-            L.orc_create.restype = ctypes.c_void_p
-            L.orc_create.argtypes = [ctypes.POINTER(OrcParams)]
-            L.orc_destroy.argtypes = [ctypes.c_void_p]
-            L.orc_init.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
-            L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
-            L.orc_get_f.argtypes = [ctypes.c_void_p, _D]
-            L.orc_set_f.argtypes = [ctypes.c_void_p, _D]
-            L.orc_get_moments.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
-            L.orc_eval.argtypes = [ctypes.c_void_p, _D, _D, _D]
-            L.orc_weno5_learned.restype = ctypes.c_double
-            L.orc_weno5_learned.argtypes = [_D, _D, _D]
-            L.orc_set_mlp.argtypes = [ctypes.c_void_p, _D]
-            L.orc_set_threads.argtypes = [ctypes.c_int]
-            L.orc_max_threads.restype = ctypes.c_int
-            _lib = L
+            _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+def source() -> str:
+    """Text of olb_oracle.c."""
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+def load_variant(text: str, directory: str):
+    """Compile a modified copy `text` of olb_oracle.c (single-threaded, same
+    rounding flags) into `directory` and return the loaded library, for tests
+    that plant a mistake in the oracle and check that a pin catches it.  Pass
+    it to Oracle(..., library=...)."""
+    src = os.path.join(directory, "variant.c")
+    out = os.path.join(directory, "libvariant.so")
+    with open(src, "w") as fh:
+        fh.write(text)
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                    "-o", out, src, "-lm"], check=True, capture_output=True)
+    return _declare(ctypes.CDLL(out))
 
 
 def _p(a: np.ndarray):
@@ -211,7 +234,8 @@ class Oracle:
 
     def __init__(self, nx, ny, ds, dt, tau, a=9.0 / 8.0, b=1.0 / 3.0,
                  sigma=1e-4, Tw=(1.0, 1.0), uw=(0.0, 0.0), side_x=0,
-                 side_y=0):
+                 side_y=0, library=None):
+        self._lib = library if library is not None else lib()
         self.nx, self.ny = int(nx), int(ny)
         p = OrcParams()
         p.nx, p.ny = self.nx, self.ny
@@ -221,14 +245,14 @@ class Oracle:
         p.uw[0], p.uw[1] = float(uw[0]), float(uw[1])
         p.side_x, p.side_y = int(side_x), int(side_y)
         self._params = p
-        h = lib().orc_create(ctypes.byref(p))
+        h = self._lib.orc_create(ctypes.byref(p))
         if not h:
             raise ValueError("oracle rejected the parameters")
         self._h = ctypes.c_void_p(h)
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().orc_destroy(self._h)
+            self._lib.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -242,32 +266,32 @@ class Oracle:
 
     def init_fields(self, n, ux, uy, T):
         arrs = [_f64(x).reshape(self._shape()) for x in (n, ux, uy, T)]
-        lib().orc_init(self._h, *[_p(a) for a in arrs])
+        self._lib.orc_init(self._h, *[_p(a) for a in arrs])
 
     def step(self, nsteps: int = 1):
-        lib().orc_step(self._h, int(nsteps))
+        self._lib.orc_step(self._h, int(nsteps))
 
     def set_mlp(self, theta=None):
         """Learned WENO weights with parameters theta (None: Jiang-Shu)."""
         if theta is None:
-            lib().orc_set_mlp(self._h, None)
+            self._lib.orc_set_mlp(self._h, None)
         else:
             self._mlp = _f64(theta)
-            lib().orc_set_mlp(self._h, _p(self._mlp))
+            self._lib.orc_set_mlp(self._h, _p(self._mlp))
 
     def moments(self):
         out = [np.zeros(self._shape()) for _ in range(4)]
-        lib().orc_get_moments(self._h, *[_p(a) for a in out])
+        self._lib.orc_get_moments(self._h, *[_p(a) for a in out])
         return tuple(out)
 
     def get_populations(self) -> np.ndarray:
         out = np.zeros((25,) + self._shape())
-        lib().orc_get_f(self._h, _p(out))
+        self._lib.orc_get_f(self._h, _p(out))
         return out
 
     def set_populations(self, f) -> None:
         f = _f64(f).reshape((25,) + self._shape())
-        lib().orc_set_f(self._h, _p(f))
+        self._lib.orc_set_f(self._h, _p(f))
 
     def evaluate(self):
         """L[f] ([25][ny][nx]) and the stage fields of the current f:
@@ -275,7 +299,7 @@ class Oracle:
         L = np.zeros((25,) + self._shape())
         f7 = np.zeros((7,) + self._shape())
         nw = np.zeros((2, self.ny))
-        lib().orc_eval(self._h, _p(L), _p(f7), _p(nw))
+        self._lib.orc_eval(self._h, _p(L), _p(f7), _p(nw))
         names = ("n", "ux", "uy", "T", "dp", "Fx", "Fy")
         out = {k: f7[i] for i, k in enumerate(names)}
         out["nw"] = nw
