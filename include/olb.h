@@ -74,10 +74,13 @@ enum {
 /* Arithmetic of the populations. */
 enum {
     OLB_FP64 = 0,       /* everything in FP64 */
-    OLB_FP32_KAHAN = 1  /* populations, fluxes and stencils in FP32; the
-                           25-velocity moment sums Kahan-compensated; u, T and
-                           Delta p recovered in double-float (hi + lo FP32)
-                           arithmetic, n and Delta p staged as hi + lo pairs */
+    OLB_FP32_KAHAN = 1  /* FP32 arithmetic with compensated storage: every
+                           population held as a pair hi + lo of floats (the
+                           same 8 bytes as FP64), fluxes and stencils in FP32
+                           on first differences of the pairs, the 25-velocity
+                           moment sums compensated (double-float), T and
+                           Delta p recovered in double-float arithmetic, the
+                           RK-3 combination in double-float arithmetic */
 };
 
 /* Non-linear WENO weights. */
@@ -177,6 +180,26 @@ int olb_moments(olb_ctx *ctx, double *n, double *ux, double *uy, double *T);
 int olb_moments_device(olb_ctx *ctx, double *n, double *ux, double *uy,
                        double *T);
 
+/* Global sums over the grid of the current populations, computed on the
+ * GPU in FP64 (FP32 contexts sum their hi + lo pairs in FP64) in a fixed
+ * order, so that repeated calls on the same state agree bit for bit:
+ *   out[0] = sum_nodes n ds^2                       (mass, Sec. 2.2)
+ *   out[1] = sum_nodes n u_x ds^2, out[2] = ... n u_y ds^2   (momentum)
+ *   out[3] = sum_nodes sum_kappa |p|^2/2 f ds^2 = sum n (T + |u|^2/2) ds^2
+ *            (kinetic energy of the particles, Eq. sigmaq_def with m = 1)
+ * out: host array of 4 doubles.  Mass is conserved between periodic sides
+ * and diffuse walls alike (zero net wall flux, Eq. nw); energy is exchanged
+ * with the walls and with the van der Waals force.  Returns after the values
+ * are in out. */
+int olb_totals(olb_ctx *ctx, double *out);
+
+/* Advance nsteps >= 0 RK-3 steps as olb_step does and record the four sums
+ * of olb_totals after every `every` >= 1 steps: out (host) receives
+ * floor(nsteps / every) records of 4 doubles, record r after (r + 1) every
+ * steps.  At most nx * ny records (OLB_ERR_ARG otherwise).  Returns the
+ * status of olb_step. */
+int olb_step_totals(olb_ctx *ctx, int nsteps, int every, double *out);
+
 /* Copy the populations to / from a host array [25][ny][nx] in FP64 (FP32
  * contexts round on set).  Used for checkpoint / resume and parity checks.
  * Both return after the copy is complete. */
@@ -196,8 +219,7 @@ int olb_profile(olb_ctx *ctx, int nsteps, double *ms, int *launches);
  * Compiled shapes (tx, ty, kp): (8,8,4), (16,8,2), (16,8,1), (32,8,1),
  * (32,16,1), (8,8,8), (7,8,8); olb_create picks one from the
  * grid size (FP64: (8,8,4), or (7,8,8) when that lowers the most nodes one
- * SM advances; FP32: (32,16,1) on grids with at least two of its tiles per
- * SM, else (8,8,8), or (8,8,4) with learned weights).  With
+ * SM advances; FP32: (8,8,8), or (8,8,4) with learned weights).  With
  * OLB_WENO_LEARNED only (8,8,4), (16,8,2), (32,16,1).  olb_set_tile returns
  * OLB_ERR_ARG for any other shape; results do not depend on the shape.
  * Not part of the paper (a tuning knob). */
@@ -299,10 +321,12 @@ int olb_set_weno_mlp(olb_ctx *ctx, const float *theta);
  *
  * f: caller-owned device array of the populations, FP64 [25][ny][nx] in the
  * exchange layout of olb_get_populations, read and overwritten in place with
- * the state after nsteps >= 0 steps; *p as for olb_create, with precision
- * OLB_FP64 and at most OLB_STATIC_MAX_NODES nodes (larger grids and other
- * precisions return OLB_ERR_ARG before any device work; invalid physics
- * returns OLB_ERR_CFL like olb_create).  The work runs on `stream` (a
+ * the state after nsteps >= 0 steps.  *p as for olb_create, restricted to:
+ * precision OLB_FP64, weno_mode OLB_WENO_JS, side_y OLB_SIDE_PERIODIC,
+ * side_x OLB_SIDE_PERIODIC or OLB_SIDE_DIFFUSE, and at most
+ * OLB_STATIC_MAX_NODES nodes.  Anything else (larger grids, FP32, learned
+ * weights, specular sides) returns OLB_ERR_ARG before any device work;
+ * invalid physics returns OLB_ERR_CFL like olb_create.  The work runs on `stream` (a
  * cudaStream_t or NULL) and the call returns after it has completed, with
  * OLB_ERR_DIVERGED if an invalid moment was met, else OLB_OK.
  *

@@ -5,10 +5,64 @@
 #include <cstring>
 #include <new>
 
+#include <cuda.h>
+#include <mutex>
+
 #include "../../include/olb.h"
 #include "olb_internal.cuh"
 
 using namespace olb;
+
+// ---------------------------------------------------------------- TMA maps
+
+namespace {
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (the library links only the CUDA runtime).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+}  // namespace
+
+bool olb::tma_encode(TmaMap *out, const void *base, bool fp64, const Geo &g, int tx, int ty)
+{
+    static_assert(sizeof(TmaMap) == sizeof(CUtensorMap), "TmaMap must hold a CUtensorMap");
+    const size_t elt = fp64 ? 8 : 4;
+    const unsigned hx = (unsigned)tx + 8, hy = (unsigned)ty + 6;
+    // the box's rows must be whole 16-byte units, and its x start x0 - 4
+    // (x0 a multiple of tx) must sit on a 16-byte boundary for every tile
+    if ((hx * elt) % 16 != 0 || ((size_t)tx * elt) % 16 != 0 || (4 * elt) % 16 != 0) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint32_t planes = fp64 ? (cuuint32_t)pop_planes<double>() : (cuuint32_t)pop_planes<float>();
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * elt, (cuuint64_t)g.plane * elt};
+    const cuuint32_t box[3] = {hx, hy, planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMap m;
+    const CUresult r = fn(&m, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                          const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    std::memcpy(out->bytes, &m, sizeof(m));
+    return true;
+}
 
 // ---------------------------------------------------------------- tables
 
@@ -69,6 +123,7 @@ void fill_tab(Tab<real> *tab, const HostTables &h, const double Tw[2], const dou
     for (int k = 0; k < NQ; ++k) {
         tab->R[k] = (real)h.R[k];
         tab->R2[k] = (real)(h.R[k] * h.R[k]);
+        tab->R2lo[k] = (real)(h.R[k] * h.R[k] - (double)tab->R2[k]);
         for (int q = 0; q < NQ; ++q) {
             tab->D[k][q] = (real)h.D[k][q];
             tab->wHe[k][q] = (real)h.wHe[k][q];
@@ -125,6 +180,7 @@ struct olb_ctx {
     float *mlp;                 // learned WENO weights: network parameters
     bool mlp_set;
     double *stage4;             // FP64 [4][ny][nx] staging for host transfers
+    double *totals;             // olb_totals: partial sums, then the sums
     struct Alloc {
         void *ptr;
         size_t bytes;
@@ -136,6 +192,8 @@ struct olb_ctx {
     cudaStream_t cap;
     cudaGraphExec_t exec1, execG;
     bool initialized;
+    TmaMap tma[3];              // TMA maps of f^n, f^(1), f^(2) for the current shape
+    bool tma_ok;                // the shape's staged rows suit TMA and the maps exist
 };
 
 static void *ctx_alloc(olb_ctx *c, size_t bytes)
@@ -188,8 +246,10 @@ static cudaError_t enqueue_stage(olb_ctx *c, int st, cudaStream_t s)
     const real *src[3] = {f0, f1, f2};
     real *dst[3] = {f1, f2, f0};
     const StageCoef coef = stage_coef(c->p.dt, st);
+    const int src_buf[3] = {0, 1, 2};
     return launch_fused(src[st], f0, dst[st], c->status, c->geo, ctx_tab<real>(c), coef, c->tx, c->ty, c->kp,
-                        c->p.weno_mode == OLB_WENO_LEARNED ? c->mlp : nullptr, s);
+                        c->p.weno_mode == OLB_WENO_LEARNED ? c->mlp : nullptr,
+                        c->tma_ok ? &c->tma[src_buf[st]] : nullptr, s);
 }
 
 template <typename real>
@@ -289,8 +349,16 @@ int olb::validate_params(const olb_params *p)
 static cudaError_t prepare_tile(olb_ctx *c)
 {
     const bool learned = c->p.weno_mode == OLB_WENO_LEARNED;
-    return is_fp64(c) ? prepare_fused((double *)nullptr, c->tx, c->ty, c->kp, learned)
-                      : prepare_fused((float *)nullptr, c->tx, c->ty, c->kp, learned);
+    cudaError_t e = is_fp64(c) ? prepare_fused((double *)nullptr, c->tx, c->ty, c->kp, learned)
+                               : prepare_fused((float *)nullptr, c->tx, c->ty, c->kp, learned);
+    if (e != cudaSuccess) return e;
+    // TMA maps of the three buffers for this shape (tiles whose region lies
+    // inside the grid then load it with one copy); without them every tile
+    // takes the per-element loads
+    c->tma_ok = true;
+    for (int k = 0; k < 3 && c->tma_ok; ++k)
+        c->tma_ok = tma_encode(&c->tma[k], c->f[k], is_fp64(c), c->geo, c->tx, c->ty);
+    return cudaSuccess;
 }
 
 // Default shape, the fastest measured on a GB300 for each precision.  FP64:
@@ -298,9 +366,10 @@ static cudaError_t prepare_tile(olb_ctx *c)
 // shared memory, so a stage has one face pass and one barrier), except that
 // small grids take 7 x 8 tiles with 8 lanes when that lowers the most nodes
 // any SM has to advance (1024 x 8: 147 tiles of 56 nodes rather than 128 of
-// 64 on 152 SMs).  FP32: 32 x 16 nodes when that still gives every SM two
-// CTAs, otherwise 8 x 8 nodes with 8 lanes (4 with learned weights), so that
-// small grids still put 8-16 warps on each busy SM.  olb_set_tile overrides.
+// 64 on 152 SMs).  FP32 (compensated pairs, twice the staged bytes of plain
+// FP32): 8 x 8 nodes with 8 lanes on every grid (4096^2: 10.2 ms per stage
+// against 11.0 for 8 x 8 x 4, 14.0 for 16 x 8 x 2 and 14.2 for 32 x 16 x 1),
+// 4 lanes with learned weights.  olb_set_tile overrides.
 static void default_tile(olb_ctx *c)
 {
     int dev = 0, sms = 0;
@@ -308,16 +377,13 @@ static void default_tile(olb_ctx *c)
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
     const bool learned = c->p.weno_mode == OLB_WENO_LEARNED;
     const bool fp64 = is_fp64(c);
-    const int big = fp64 ? 0 : 4;  // indices into TILE_*
-    const int small = fp64 || learned ? 0 : 5;
     const int narrow = 6;
     auto tiles = [&](int k) {
         return (long long)((c->geo.nx + TILE_X[k] - 1) / TILE_X[k]) * ((c->geo.ny + TILE_Y[k] - 1) / TILE_Y[k]);
     };
     auto most_nodes = [&](int k) { return (tiles(k) + sms - 1) / sms * TILE_X[k] * TILE_Y[k]; };
-    int k = small;
-    if (tiles(big) >= 2 * sms) k = big;
-    else if (fp64 && !learned && most_nodes(narrow) < most_nodes(small)) k = narrow;
+    int k = fp64 || learned ? 0 : 5;
+    if (fp64 && !learned && most_nodes(narrow) < most_nodes(0)) k = narrow;
     c->tx = TILE_X[k];
     c->ty = TILE_Y[k];
     c->kp = TILE_K[k];
@@ -360,14 +426,16 @@ extern "C" int olb_create(const olb_params *p, void *stream, olb_ctx **out)
     fill_tab<double>(&c->tab64, h, p->Tw, p->uw);
     fill_tab<float>(&c->tab32, h, p->Tw, p->uw);
     c->elt = is_fp64(c) ? sizeof(double) : sizeof(float);
-    const size_t pop = (size_t)NK * g.plane * c->elt;
+    const size_t pop = (size_t)(is_fp64(c) ? pop_planes<double>() : pop_planes<float>()) * g.plane * c->elt;
     const size_t N = (size_t)g.nx * g.ny;
     for (int k = 0; k < 3; ++k) c->f[k] = ctx_alloc(c, pop);
     c->status = (int *)ctx_alloc(c, 256);
     c->stage4 = (double *)ctx_alloc(c, 4 * N * sizeof(double));
     c->mlp = p->weno_mode == OLB_WENO_LEARNED ? (float *)ctx_alloc(c, 1348 * sizeof(float)) : nullptr;
+    // olb_totals: TOTALS_BLOCKS x 4 partial sums, then the 4 sums
+    c->totals = (double *)ctx_alloc(c, (size_t)(4 * TOTALS_BLOCKS + 4) * sizeof(double));
     default_tile(c);
-    bool ok = c->f[0] && c->f[1] && c->f[2] && c->status && c->stage4 &&
+    bool ok = c->f[0] && c->f[1] && c->f[2] && c->status && c->stage4 && c->totals &&
               (p->weno_mode != OLB_WENO_LEARNED || c->mlp);
     cudaError_t e = cudaSuccess;
     if (ok) {
@@ -419,7 +487,7 @@ struct DeviceGuard {
 static int init_from_device(olb_ctx *c, const double *n, const double *ux, const double *uy, const double *T)
 {
     cudaError_t e = is_fp64(c) ? launch_init((double *)c->f[0], n, ux, uy, T, c->geo, c->tab64, c->stream)
-                               : launch_init((float *)c->f[0], n, ux, uy, T, c->geo, c->tab32, c->stream);
+                               : launch_init((float *)c->f[0], n, ux, uy, T, c->geo, c->tab64, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) return cuda_status(e);
     c->initialized = true;
@@ -513,7 +581,7 @@ extern "C" int olb_get_status(olb_ctx *c)
     cudaError_t e = cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    return h ? OLB_ERR_DIVERGED : OLB_OK;
+    return (h & 2) ? OLB_ERR_TIMEOUT : (h ? OLB_ERR_DIVERGED : OLB_OK);
 }
 
 extern "C" int olb_step(olb_ctx *c, int nsteps)
@@ -526,7 +594,7 @@ extern "C" int olb_step(olb_ctx *c, int nsteps)
 static int moments_device(olb_ctx *c, double *n, double *ux, double *uy, double *T)
 {
     cudaError_t e = is_fp64(c) ? launch_moments_out((const double *)c->f[0], n, ux, uy, T, c->geo, c->tab64, c->stream)
-                               : launch_moments_out((const float *)c->f[0], n, ux, uy, T, c->geo, c->tab32, c->stream);
+                               : launch_moments_out((const float *)c->f[0], n, ux, uy, T, c->geo, c->tab64, c->stream);
     return cuda_status(e);
 }
 
@@ -562,6 +630,51 @@ extern "C" int olb_moments(olb_ctx *c, double *n, double *ux, double *uy, double
         if (staged[k]) e = cudaMemcpyAsync(host[k], dev[k], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return cuda_status(e);
+}
+
+// Global sums of the current populations (FP64, fixed order) into device
+// out[4] on the context's stream.
+static cudaError_t enqueue_totals(olb_ctx *c, double *out)
+{
+    double *partial = c->totals;
+    return is_fp64(c) ? launch_totals((const double *)c->f[0], partial, out, c->geo, c->tab64, c->stream)
+                      : launch_totals((const float *)c->f[0], partial, out, c->geo, c->tab64, c->stream);
+}
+
+extern "C" int olb_totals(olb_ctx *c, double *out)
+{
+    if (!c || !out) return OLB_ERR_ARG;
+    if (!c->initialized) return OLB_ERR_STATE;
+    DeviceGuard dg(c->device);
+    double *dev = c->totals + 4 * TOTALS_BLOCKS;
+    cudaError_t e = enqueue_totals(c, dev);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_status(e);
+}
+
+extern "C" int olb_step_totals(olb_ctx *c, int nsteps, int every, double *out)
+{
+    if (!c || !out || nsteps < 0 || every < 1) return OLB_ERR_ARG;
+    if (!c->initialized) return OLB_ERR_STATE;
+    if (c->p.weno_mode == OLB_WENO_LEARNED && !c->mlp_set) return OLB_ERR_STATE;
+    const long long nrec = nsteps / every;
+    if (4 * nrec > 4LL * c->geo.nx * c->geo.ny) return OLB_ERR_ARG;
+    DeviceGuard dg(c->device);
+    // the records go to the staging buffer (4 per record), read back at the end
+    for (long long r = 0; r < nrec; ++r) {
+        int rc = olb_step_async(c, every);
+        if (rc != OLB_OK) return rc;
+        cudaError_t e = enqueue_totals(c, c->stage4 + 4 * r);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    int rc = olb_step_async(c, nsteps - (int)(nrec * every));
+    if (rc != OLB_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    if (nrec > 0)
+        e = cudaMemcpyAsync(out, c->stage4, (size_t)(4 * nrec) * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return olb_get_status(c);
 }
 
 extern "C" int olb_get_populations(olb_ctx *c, double *f)

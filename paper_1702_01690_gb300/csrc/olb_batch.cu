@@ -214,7 +214,7 @@ extern "C" int olb_batch_create(const olb_params *runs, int count, void *stream,
         fill_tab<double>(&b->tab64[r], h, p->Tw, p->uw);
         fill_tab<float>(&b->tab32[r], h, p->Tw, p->uw);
         b->off[r] = acc;
-        acc += ((long long)NK * g.plane + 63) / 64 * 64;
+        acc += ((long long)(b_fp64(b) ? pop_planes<double>() : pop_planes<float>()) * g.plane + 63) / 64 * 64;
         b->max_nodes = std::max(b->max_nodes, (long long)g.nx * g.ny);
     }
     b->total_elems = acc;
@@ -283,7 +283,7 @@ extern "C" int olb_batch_init_fields(olb_batch *b, int run, const double *n, con
         e = b_fp64(b) ? launch_init((double *)b->f[0] + b->off[run], b->stage4, b->stage4 + N, b->stage4 + 2 * N,
                                     b->stage4 + 3 * N, g, b->tab64[run], b->stream)
                       : launch_init((float *)b->f[0] + b->off[run], b->stage4, b->stage4 + N, b->stage4 + 2 * N,
-                                    b->stage4 + 3 * N, g, b->tab32[run], b->stream);
+                                    b->stage4 + 3 * N, g, b->tab64[run], b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status + run, 0, sizeof(int), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -354,7 +354,7 @@ extern "C" int olb_batch_moments(olb_batch *b, int run, double *n, double *ux, d
                                                    host[3] ? dev[3] : nullptr, g, b->tab64[run], b->stream)
                               : launch_moments_out((const float *)b->f[0] + b->off[run], host[0] ? dev[0] : nullptr,
                                                    host[1] ? dev[1] : nullptr, host[2] ? dev[2] : nullptr,
-                                                   host[3] ? dev[3] : nullptr, g, b->tab32[run], b->stream);
+                                                   host[3] ? dev[3] : nullptr, g, b->tab64[run], b->stream);
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
         if (host[k]) e = cudaMemcpyAsync(host[k], dev[k], N * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

@@ -3,15 +3,16 @@
 //
 // One CTA owns a TX x TY tile of nodes and stages the populations of the
 // tile plus a 3-node halo on every side in shared memory:
-//   1. load f_s for the (TX+8) x (TY+6) region (x offset -4 keeps rows
-//      16-byte aligned for vector loads; y and periodic x wrap);
+//   1. load f_s for the (TX+8) x (TY+6) region (x offset -4 keeps the rows
+//      of the region 16-byte aligned; y and periodic x wrap);
 //   2. moments n, u, T, Delta p at every fluid node of the region (Sec. 2.2,
 //      Eq. vdw), with the even reflection of Delta p and n at walls
 //      (Sec. 3.4.3);
 //   3. walls (Sec. 3.4.2): extrapolated ghosts for the outgoing velocities,
-//      the WENO flux of those velocities at the wall face, summed over the
-//      10 velocities with warp shuffles into n_w (Eq. nw), and f^eq_w ghosts
-//      for the incoming velocities;
+//      the WENO flux of those velocities at the wall face, summed per tile
+//      row into n_w (Eq. nw) by a warp-shuffle reduction over the half-warp
+//      that computes the row's ten fluxes, and f^eq_w ghosts for the
+//      incoming velocities;
 //   4. force F = grad(Delta p)/n + sigma grad(Laplacian n) at the tile nodes
 //      from the 49-point stencils (Eqs. F_def, stencil_grad, stencil_glap);
 //   5. for KP velocities at a time (one lane of TX*TY threads, rounded up to
@@ -20,6 +21,15 @@
 //      flux differences, the momentum derivative (Eq. derf), BGK with f^eq
 //      (Eqs. feq, g_alpha) and the RK-3 combination of Eq. rk3, written to
 //      the output buffer.  KP > 1 gives small tiles enough warps.
+//
+// FP32 (real = float) keeps every population as a pair hi + lo of floats
+// (compensated storage, olb_kernels.cuh): the staged region holds both parts,
+// moments are summed in double-float arithmetic, a face stores only its WENO
+// correction (the face value minus its upwind node, a function of first
+// differences of pairs) so that flux differences are first differences too,
+// the collision uses the equilibrium split into its exactly symmetric and
+// antisymmetric parts in p (no FP32 rounding of f^eq or of f/tau changes the
+// momentum), and the RK-3 combination is done in double-float arithmetic.
 #pragma once
 
 #include "olb_mlp.cuh"
@@ -51,6 +61,15 @@ __device__ __forceinline__ float field_diff(float2 a, float2 b) { return (a.x - 
 __device__ __forceinline__ double field_val(double a) { return a; }
 __device__ __forceinline__ float field_val(float2 a) { return a.x + a.y; }
 
+// lo parts of the staged populations (FP32 only; FP64 has none)
+template <typename real, int HY, int HX>
+struct PopLo {
+    real lo[NK][HY][HX];
+};
+template <int HY, int HX>
+struct PopLo<double, HY, HX> {
+};
+
 template <typename real, int TX, int TY, int KP>
 struct FusedSmem {
     // LS: threads per velocity lane, the tile's nodes rounded up to whole
@@ -58,17 +77,26 @@ struct FusedSmem {
     static constexpr int HX = TX + 8, HY = TY + 6, NN = TX * TY, LS = (NN + 31) / 32 * 32, NT = LS * KP;
     using fld = typename FieldT<real>::type;
     real pop[NK][HY][HX];
+    PopLo<real, HY, HX> pl;
     fld n[HY][HX];
     fld dp[HY][HX];
     real ux[TY][TX];
     real uy[TY][TX];
-    real T[TY][TX];
+    fld T[TY][TX];  // FP32: hi + lo pair
+    // FP32: e = sum |p|^2 f at the tile nodes as a double-float pair (the
+    // target energy of the equilibrium's correction); unused in FP64
+    fld eng[sizeof(real) == 4 ? TY : 1][sizeof(real) == 4 ? TX : 1];
     // per tile node, shared by the KP velocity lanes (with one lane they stay
     // in registers): the stencil sums of grad(Delta p) and grad(Laplacian n),
-    // inv_ds / n, E_q = (c/tau) n g_q(u_x, T) and g_q(u_y, T)
-    // (and, on tiles that keep every face, G_x = c F_x and G_y in L_G, L_G + 1)
-    static constexpr int L_DDX = 0, L_DDY = 1, L_LDX = 2, L_LDY = 3, L_DN = 4, L_E = 5, L_GY = 5 + NQ, L_G = 5 + 2 * NQ;
-    real loc[KP > 1 ? 7 + 2 * NQ : 1][KP > 1 ? NN : 1];
+    // inv_ds / n, E_q = (c/tau) n g_q(u_x, T) and g_q(u_y, T) (FP32: the
+    // even and odd parts n ge_q(u_x, T), n go_q(u_x, T), ge_q(u_y, T),
+    // go_q(u_y, T) instead), and, on tiles that keep every face, G_x = c F_x
+    // and G_y in L_G, L_G + 1
+    static constexpr int NEQ = sizeof(real) == 8 ? 2 : 4;  // equilibrium factor sets
+    static constexpr int L_DDX = 0, L_DDY = 1, L_LDX = 2, L_LDY = 3, L_DN = 4, L_E = 5, L_GY = 5 + NQ,
+                         L_OX = 5 + 2 * NQ, L_OY = 5 + 3 * NQ, L_G = 5 + NEQ * NQ,
+                         L_CA = 7 + NEQ * NQ, L_CB = 8 + NEQ * NQ, L_CC = 9 + NEQ * NQ;  // FP32: the correction
+    real loc[KP > 1 ? 7 + NEQ * NQ + (sizeof(real) == 4 ? 3 : 0) : 1][KP > 1 ? NN : 1];
     // WENO-5 face values.  Small tiles (at most 64 nodes) hold the faces of
     // all 25 velocities, so one pass computes them all and the node updates
     // follow without further barriers; larger tiles hold KP velocities'.
@@ -76,12 +104,13 @@ struct FusedSmem {
     static constexpr int KF = ALL_FACES ? NK : KP;
     union {
         real fx[KF][TY][TX + 1];
-        // wall-face flux of each outgoing velocity (10) in each tile row, left
-        // and right diffuse wall: written and read between the moments and the
-        // force, before any face value is stored
-        real wflux[2][TY][10];
+        // wall density n_w of each tile row at the left and right diffuse wall
+        // (Eq. nw): written and read between the moments and the force,
+        // before any face value is stored
+        real wnw[2][TY];
     };
     real fy[KF][TY + 1][TX];
+    unsigned long long mbar;  // completion barrier of the TMA copy of phase 1
 };
 
 template <typename real>
@@ -106,15 +135,84 @@ __device__ __forceinline__ real face_value(const float *mlp, real v0, real v1, r
         return weno5(v0, v1, v2, v3, v4);
 }
 
+// FP32 pairs: the correction c (face value minus the upwind node v2) of the
+// stencil with first differences d01 .. d34.
+template <bool LEARNED>
+__device__ __forceinline__ float face_corr(const float *mlp, float d01, float d12, float d23, float d34)
+{
+    if constexpr (LEARNED)
+        return weno5_learned_corr(mlp, d01, d12, d23, d34);
+    else
+        return weno5_corr(d01, d12, d23, d34);
+}
+
+// ---------------------------------------------------------------- TMA staging
+// Iterations of the bounded wait for the copy (each try_wait suspends for at
+// most a short, hardware-defined time): far above the microseconds a copy of
+// a tile's region takes, far below a hang.
+constexpr int TMA_WAIT_LIMIT = 1 << 16;
+
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity)
+{
+    for (int i = 0; i < TMA_WAIT_LIMIT; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Phase 1 for a tile whose staged region lies inside the grid: one TMA copy
+// of the box (HX, HY, planes) at (gx0, gy0, 0) of the tensor map into the
+// staging arrays (pop, then the lo planes in FP32, contiguous in FusedSmem in
+// the box's order), completion tracked by an mbarrier.  If the bounded wait
+// runs out, bit 1 of the status word is set, the copy is waited for once more
+// (bounded) and false is returned: the caller leaves the tile untouched.
+template <typename real, int TX, int TY, int KP>
+__device__ __forceinline__ bool tma_stage(FusedSmem<real, TX, TY, KP> &sm, const TmaMap *tmap, int gx0, int gy0,
+                                          int *status)
+{
+    constexpr unsigned bytes = sizeof(sm.pop) + (sizeof(real) == 4 ? sizeof(sm.pop) : 0);
+    const unsigned mbar = (unsigned)__cvta_generic_to_shared(&sm.mbar);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(&sm.pop[0][0][0]);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];" ::"r"(dst),
+            "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(gx0), "r"(gy0), "r"(0), "r"(mbar)
+            : "memory");
+    }
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    const bool ok = mbar_wait(mbar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(status, 2);
+        mbar_wait(mbar, 0);
+        return false;
+    }
+    return true;
+}
+
 // One stage for the tile whose lower-left node is (x0, y0); all threads of
-// the CTA call it (it synchronises).  g and t may live in parameter space
+// the CTA call it (it synchronises).  ca, cb, cc: the stage's coefficients of
+// f^n, f_s and dt L (Eq. rk3), in the population precision; ca_lo, cb_lo:
+// their remainders (FP32: 1/3 and 2/3 as double-float constants; 0 in FP64).
+// tmap: TMA map of fs for this tile shape (single grids), or nullptr.  g and t may live in parameter space
 // (single grid) or shared memory (batch); mlp: the learned network's
 // parameters in shared memory (LEARNED only).
 template <typename real, int TX, int TY, int KP, bool LEARNED = false>
 __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, const real *__restrict__ fs,
                                            const real *fn, real *out, int *__restrict__ status, const Geo &g,
                                            const Tab<real> &t, const int x0, const int y0, const real ca,
-                                           const real cb, const real cc, const float *mlp = nullptr)
+                                           const real cb, const real cc, const real ca_lo, const real cb_lo,
+                                           const float *mlp = nullptr, const TmaMap *tmap = nullptr)
 {
     using S = FusedSmem<real, TX, TY, KP>;
     constexpr int NT = S::NT, NN = S::NN, HX = S::HX, HY = S::HY;
@@ -127,52 +225,65 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     const bool active = (node < NN) && (i < g.nx) && (j < g.ny);
 
     // ---- 1. populations of the region (c <-> x = x0 - 4 + c, r <-> y = y0 - 3 + r)
-    //    Periodic sides wrap.  Ghost layers 0..2 of a specular side hold the
+    //    A region inside the grid comes in one TMA copy.  Otherwise:
+    //    periodic sides wrap.  Ghost layers 0..2 of a specular side hold the
     //    populations of the first three nodes inside with the normal
     //    velocity component reversed (Sec. 3.4.1); diffuse-wall ghosts are
     //    set in phase 3; anything further out is never read and holds 0.
-    for (int e = tid; e < HY * HX; e += NT) {
-        const int r = e / HX, c = e - r * HX;
-        int gy = y0 - 3 + r, gx = x0 - 4 + c;
-        bool flip_x = false, flip_y = false, zero = false;
-        if (gy < 0 || gy >= g.ny) {
-            if (!g.spec_y) {
-                gy = wrap(gy, g.ny);
-            } else if ((gy < 0 ? -1 - gy : gy - g.ny) <= 2) {
-                gy = gy < 0 ? -1 - gy : 2 * g.ny - 1 - gy;
-                flip_y = true;
-            } else {
-                zero = true;
-            }
-        }
-        if (gx < 0 || gx >= g.nx) {
-            const bool lo = gx < 0;
-            if (!g.walls) {
-                gx = wrap(gx, g.nx);
-            } else if ((lo ? g.spec_lo : g.spec_hi) && (lo ? -1 - gx : gx - g.nx) <= 2) {
-                gx = lo ? -1 - gx : 2 * g.nx - 1 - gx;
-                flip_x = true;
-            } else {
-                zero = true;
-            }
-        }
-        if (zero) {
-#pragma unroll 5
-            for (int k = 0; k < NK; ++k) sm.pop[k][r][c] = real(0);
-            continue;
-        }
-        const real *src = fs + (long long)gy * g.pitch + gx;
-        if (!flip_x && !flip_y) {
-#pragma unroll 5
-            for (int k = 0; k < NK; ++k) sm.pop[k][r][c] = __ldg(src + k * g.plane);
-        } else {
-#pragma unroll
-            for (int k1 = 0; k1 < NQ; ++k1)
-#pragma unroll
-                for (int k2 = 0; k2 < NQ; ++k2) {
-                    const int kk = NQ * (flip_x ? NQ - 1 - k1 : k1) + (flip_y ? NQ - 1 - k2 : k2);
-                    sm.pop[NQ * k1 + k2][r][c] = __ldg(src + kk * g.plane);
+    const bool inside = tmap != nullptr && x0 >= 4 && x0 + TX + 4 <= g.nx && y0 >= 3 && y0 + TY + 3 <= g.ny;
+    if (inside) {
+        if (!tma_stage(sm, tmap, x0 - 4, y0 - 3, status)) return;
+    } else {
+        for (int e = tid; e < HY * HX; e += NT) {
+            const int r = e / HX, c = e - r * HX;
+            int gy = y0 - 3 + r, gx = x0 - 4 + c;
+            bool flip_x = false, flip_y = false, zero = false;
+            if (gy < 0 || gy >= g.ny) {
+                if (!g.spec_y) {
+                    gy = wrap(gy, g.ny);
+                } else if ((gy < 0 ? -1 - gy : gy - g.ny) <= 2) {
+                    gy = gy < 0 ? -1 - gy : 2 * g.ny - 1 - gy;
+                    flip_y = true;
+                } else {
+                    zero = true;
                 }
+            }
+            if (gx < 0 || gx >= g.nx) {
+                const bool lo = gx < 0;
+                if (!g.walls) {
+                    gx = wrap(gx, g.nx);
+                } else if ((lo ? g.spec_lo : g.spec_hi) && (lo ? -1 - gx : gx - g.nx) <= 2) {
+                    gx = lo ? -1 - gx : 2 * g.nx - 1 - gx;
+                    flip_x = true;
+                } else {
+                    zero = true;
+                }
+            }
+            if (zero) {
+#pragma unroll 5
+                for (int k = 0; k < NK; ++k) {
+                    sm.pop[k][r][c] = real(0);
+                    if constexpr (sizeof(real) == 4) sm.pl.lo[k][r][c] = 0.0f;
+                }
+                continue;
+            }
+            const real *src = fs + (long long)gy * g.pitch + gx;
+            if (!flip_x && !flip_y) {
+#pragma unroll 5
+                for (int k = 0; k < NK; ++k) {
+                    sm.pop[k][r][c] = __ldg(src + k * g.plane);
+                    if constexpr (sizeof(real) == 4) sm.pl.lo[k][r][c] = __ldg(src + (NK + k) * g.plane);
+                }
+            } else {
+#pragma unroll
+                for (int k1 = 0; k1 < NQ; ++k1)
+#pragma unroll
+                    for (int k2 = 0; k2 < NQ; ++k2) {
+                        const int kk = NQ * (flip_x ? NQ - 1 - k1 : k1) + (flip_y ? NQ - 1 - k2 : k2);
+                        sm.pop[NQ * k1 + k2][r][c] = __ldg(src + kk * g.plane);
+                        if constexpr (sizeof(real) == 4) sm.pl.lo[NQ * k1 + k2][r][c] = __ldg(src + (NK + kk) * g.plane);
+                    }
+            }
         }
     }
     __syncthreads();
@@ -193,7 +304,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     const bool right_wall = x_hi && g.wall_hi;
     // wall-flux items start on the first warp after the moment positions
     constexpr int e_flux = (HY * (HX - 2) + 31) / 32 * 32;
-    const int nflux = ((int)left_wall + (int)right_wall) * TY * 10;
+    const int nflux = ((int)left_wall + (int)right_wall) * TY * 16;
     for (int e = tid; e < HY * (HX - 2); e += NT) {
         const int r = e / (HX - 2), c = e - r * (HX - 2) + 1;
         const int gx = x0 - 4 + c, gyr = y0 - 3 + r;
@@ -242,7 +353,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             if (tile_node) {
                 sm.ux[tr][tc] = (real)ux;
                 sm.uy[tr][tc] = (real)uy;
-                sm.T[tr][tc] = (real)T;
+                sm.T[tr][tc] = T;
                 if (own) {
                     const bool ok = (n > 0.0) && (T > 0.0) && (g.b * n < 1.0) && isfinite(n) && isfinite(T) &&
                                     isfinite(ux) && isfinite(uy);
@@ -250,63 +361,123 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 }
             }
         } else {
-            Kahan kn{0.f, 0.f}, kx{0.f, 0.f}, ky{0.f, 0.f}, ke{0.f, 0.f};
+            // FP32, compensated storage: row and column sums of the 5 x 5 pairs
+            // as double-float values; n and e = sum |p|^2 f from them in
+            // double-float arithmetic.  j needs FP32 accuracy of j itself:
+            // R_4 (sx_4 - sx_0) + R_3 (sx_3 - sx_1) with the differences of
+            // the double-float sums (R_0 = -R_4, R_1 = -R_3, R_2 = 0).
+            f2 sx[NQ], sy[NQ];
+            {
+                float h[NQ], l[NQ];
 #pragma unroll
-            for (int k1 = 0; k1 < NQ; ++k1)
+                for (int k1 = 0; k1 < NQ; ++k1) {
+#pragma unroll
+                    for (int k2 = 0; k2 < NQ; ++k2) {
+                        h[k2] = sm.pop[NQ * k1 + k2][r][c];
+                        l[k2] = sm.pl.lo[NQ * k1 + k2][r][c];
+                    }
+                    sx[k1] = pair_sum5(h, l);
+                }
 #pragma unroll
                 for (int k2 = 0; k2 < NQ; ++k2) {
-                    const float v = (float)sm.pop[NQ * k1 + k2][r][c];
-                    kn.add(v);
-                    kx.add((float)t.R[k1] * v);
-                    ky.add((float)t.R[k2] * v);
-                    ke.add(((float)t.R2[k1] + (float)t.R2[k2]) * v);
+#pragma unroll
+                    for (int k1 = 0; k1 < NQ; ++k1) {
+                        h[k1] = sm.pop[NQ * k1 + k2][r][c];
+                        l[k1] = sm.pl.lo[NQ * k1 + k2][r][c];
+                    }
+                    sy[k2] = pair_sum5(h, l);
                 }
-            // the compensated sums as double-float values; u, T and
-            // Delta p = n T - p^w = n^2 (a - b T / (1 - b n)) (Eq. vdw) in
-            // double-float arithmetic, so that the stencils of n and Delta p
-            // see ~44-bit values without the FP64 pipe
+            }
             const f2 one{1.0f, 0.0f};
-            const f2 N = f2_from_kahan(kn), IN = f2_div(one, N);
-            const f2 UX = f2_mul(f2_from_kahan(kx), IN), UY = f2_mul(f2_from_kahan(ky), IN);
-            const f2 U2 = f2_add(f2_mul(UX, UX), f2_mul(UY, UY));
-            const f2 T = f2_scale(f2_add(f2_mul(f2_from_kahan(ke), IN), f2_neg(U2)), 0.5f);
+            const f2 N = f2_add(f2_add(f2_add(sx[0], sx[4]), f2_add(sx[1], sx[3])), sx[2]);
+            const float jx = fmaf((float)t.R[4], pdiff(sx[4].hi, sx[4].lo, sx[0].hi, sx[0].lo),
+                                  (float)t.R[3] * pdiff(sx[3].hi, sx[3].lo, sx[1].hi, sx[1].lo));
+            const float jy = fmaf((float)t.R[4], pdiff(sy[4].hi, sy[4].lo, sy[0].hi, sy[0].lo),
+                                  (float)t.R[3] * pdiff(sy[3].hi, sy[3].lo, sy[1].hi, sy[1].lo));
+            const f2 S4 = f2_add(f2_add(sx[0], sx[4]), f2_add(sy[0], sy[4]));
+            const f2 S3 = f2_add(f2_add(sx[1], sx[3]), f2_add(sy[1], sy[3]));
+            const f2 R24{(float)t.R2[4], (float)t.R2lo[4]}, R23{(float)t.R2[3], (float)t.R2lo[3]};
+            const f2 Ea = f2_cmul(R24, S4.hi, S4.lo), Eb = f2_cmul(R23, S3.hi, S3.lo);
+            const f2 E = f2_add(fast_two_sum(Ea.hi, Ea.lo), fast_two_sum(Eb.hi, Eb.lo));
+            // u, T and Delta p = n T - p^w = n^2 (a - b T / (1 - b n)) (Eq. vdw):
+            // T and Delta p in double-float arithmetic, so that the stencils of
+            // n and Delta p see ~44-bit values without the FP64 pipe
+            const f2 IN = f2_div(one, N);
+            const float UX = jx * IN.hi, UY = jy * IN.hi;
+            const f2 T = f2_scale(f2_add_f(f2_mul(E, IN), -fmaf(UX, UX, UY * UY)), 0.5f);
             const f2 BN = f2_mul(vdw_b, N);
             const f2 Q = f2_div(f2_mul(vdw_b, T), f2_add(one, f2_neg(BN)));
             const f2 DP = f2_mul(f2_mul(N, N), f2_add(vdw_a, f2_neg(Q)));
             sm.n[r][c] = make_float2(N.hi, N.lo);
             sm.dp[r][c] = make_float2(DP.hi, DP.lo);
             if (tile_node) {
-                sm.ux[tr][tc] = UX.hi;
-                sm.uy[tr][tc] = UY.hi;
-                sm.T[tr][tc] = T.hi;
+                sm.ux[tr][tc] = UX;
+                sm.uy[tr][tc] = UY;
+                sm.T[tr][tc] = make_float2(T.hi, T.lo);
+                sm.eng[tr][tc] = make_float2(E.hi, E.lo);
                 if (own) {
                     const bool ok = (N.hi > 0.0f) && (T.hi > 0.0f) && (BN.hi < 1.0f) && isfinite(N.hi) &&
-                                    isfinite(T.hi) && isfinite(UX.hi) && isfinite(UY.hi);
+                                    isfinite(T.hi) && isfinite(UX) && isfinite(UY);
                     if (!ok) atomicOr(status, 1);
                 }
             }
         }
     }
     // wall flux item f runs on thread (e_flux + f) mod NT: on the warps after
-    // those with moment positions
+    // those with moment positions.  Each tile row of a wall takes a
+    // half-warp: lanes v = 0..9 compute the flux of outgoing velocity v (the
+    // half-range p_x < 0 at x = 0, p_x > 0 at x = nx ds), lanes 10..15 add 0,
+    // and a shuffle reduction over the half-warp gives the row's sum.  (e_flux
+    // and NT are multiples of 32, so f runs over whole half-warps.)
     for (int f = (tid - e_flux % NT + NT) % NT; f < nflux; f += NT) {
         // (wall, tile row tr, outgoing velocity v); the left wall's items first
-        const int side = (f >= TY * 10 || !left_wall) ? 1 : 0;
-        const int fr = f >= TY * 10 ? f - TY * 10 : f;
-        const int tr = fr / 10, v = fr - 10 * (fr / 10);
+        const int side = (f >= TY * 16 || !left_wall) ? 1 : 0;
+        const int fr = f >= TY * 16 ? f - TY * 16 : f;
+        const int tr = fr >> 4, v = fr & 15;
         const int k1 = side ? 3 + v / 5 : v / 5;
         const int k = NQ * k1 + v % 5;
         // nearest three fluid nodes, nearest first; ghost layers 0 and 1
         // are the next two columns outwards
         const int c0 = side ? g.nx - 1 - (x0 - 4) : 0 - (x0 - 4);
         const int dc = side ? -1 : 1;
-        const real a0 = sm.pop[k][tr + 3][c0], a1 = sm.pop[k][tr + 3][c0 + dc];
-        const real a2 = sm.pop[k][tr + 3][c0 + 2 * dc];
-        const real g0 = fma(real(3), a0 - a1, a2);
-        const real g1 = fma(real(6), a0, fma(real(-8), a1, real(3) * a2));
-        if (c0 - dc >= 0 && c0 - dc < HX) sm.pop[k][tr + 3][c0 - dc] = g0;
-        if (c0 - 2 * dc >= 0 && c0 - 2 * dc < HX) sm.pop[k][tr + 3][c0 - 2 * dc] = g1;
-        sm.wflux[side][tr][v] = t.R[k1] * face_value<real, LEARNED>(mlp, a2, a1, a0, g0, g1);
+        real wf = 0;
+        if (v >= 10) {
+            // idle lane of the row's half-warp
+        } else if constexpr (sizeof(real) == 8) {
+            const real a0 = sm.pop[k][tr + 3][c0], a1 = sm.pop[k][tr + 3][c0 + dc];
+            const real a2 = sm.pop[k][tr + 3][c0 + 2 * dc];
+            const real g0 = fma(real(3), a0 - a1, a2);
+            const real g1 = fma(real(6), a0, fma(real(-8), a1, real(3) * a2));
+            if (c0 - dc >= 0 && c0 - dc < HX) sm.pop[k][tr + 3][c0 - dc] = g0;
+            if (c0 - 2 * dc >= 0 && c0 - 2 * dc < HX) sm.pop[k][tr + 3][c0 - 2 * dc] = g1;
+            wf = t.R[k1] * face_value<real, LEARNED>(mlp, a2, a1, a0, g0, g1);
+        } else {
+            // pairs: the ghosts 3a0 - 3a1 + a2 and 6a0 - 8a1 + 3a2 as a0 plus
+            // combinations of the differences D1 = a0 - a1, D2 = a1 - a2, and
+            // the stencil (a2, a1, a0, g0, g1) by its first differences
+            // (D2, D1, 2 D1 - D2, 3 D1 - 2 D2)
+            const int row = tr + 3;
+            const float h0 = sm.pop[k][row][c0], l0 = sm.pl.lo[k][row][c0];
+            const float h1 = sm.pop[k][row][c0 + dc], l1 = sm.pl.lo[k][row][c0 + dc];
+            const float h2 = sm.pop[k][row][c0 + 2 * dc], l2 = sm.pl.lo[k][row][c0 + 2 * dc];
+            const float D1 = pdiff(h0, l0, h1, l1), D2 = pdiff(h1, l1, h2, l2);
+            const float e0 = fmaf(2.0f, D1, -D2), e1 = fmaf(5.0f, D1, -3.0f * D2);
+            const f2 G0 = f2_add_f(f2{h0, l0}, e0), G1 = f2_add_f(f2{h0, l0}, e1);
+            if (c0 - dc >= 0 && c0 - dc < HX) {
+                sm.pop[k][row][c0 - dc] = G0.hi;
+                sm.pl.lo[k][row][c0 - dc] = G0.lo;
+            }
+            if (c0 - 2 * dc >= 0 && c0 - 2 * dc < HX) {
+                sm.pop[k][row][c0 - 2 * dc] = G1.hi;
+                sm.pl.lo[k][row][c0 - 2 * dc] = G1.lo;
+            }
+            const float corr = face_corr<LEARNED>(mlp, D2, D1, e0, fmaf(3.0f, D1, -2.0f * D2));
+            wf = t.R[k1] * (h0 + (l0 + corr));
+        }
+        const unsigned half = (tid & 16) ? 0xffff0000u : 0x0000ffffu;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) wf += __shfl_xor_sync(half, wf, o);
+        if (v == 0) sm.wnw[side][tr] = -wf * t.inv_den[side];
     }
 
     // ---- 3. sides: n and Delta p reflected evenly into the ghost layers of
@@ -349,11 +520,9 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 const int tr = fr / 30, m = (fr - 30 * tr) / 10, v = fr - 30 * tr - 10 * m;
                 const int c = side ? g.nx + m - (x0 - 4) : -1 - m - (x0 - 4);
                 if (c < 0 || c >= HX) continue;
-                real flux = sm.wflux[side][tr][0];
-#pragma unroll
-                for (int q = 1; q < 10; ++q) flux += sm.wflux[side][tr][q];
                 const int k = NQ * (side ? v / 5 : 3 + v / 5) + v % 5;
-                sm.pop[k][tr + 3][c] = (-flux * t.inv_den[side]) * t.geqw[side][k];
+                sm.pop[k][tr + 3][c] = sm.wnw[side][tr] * t.geqw[side][k];
+                if constexpr (sizeof(real) == 4) sm.pl.lo[k][tr + 3][c] = 0.0f;
             }
         }
     }
@@ -380,24 +549,83 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     };
     auto glap_sum = [&](bool along_x) {
         real acc = 0;
+        if constexpr (sizeof(real) == 4) {
+            // FP32: the stencil cancels its O(ds) terms down to O(ds^3) (a
+            // factor ~1/(ds k)^2 on fine grids), so the weighted differences
+            // are summed in double-float arithmetic with double-float weights
+            // (exact products of the hi parts, TwoSum accumulation): the sum
+            // keeps FP32 accuracy of itself, not of its terms
+            f2 sum{0.0f, 0.0f};
 #pragma unroll
-        for (int l = 1; l <= 3; ++l)
+            for (int l = 1; l <= 3; ++l)
 #pragma unroll
-            for (int m = -3; m <= 3; ++m) {
-                const int am = m < 0 ? -m : m;
-                if (glap_c(am, l) != 0.0) {
-                    const real w = real(glap_c(am, l));
-                    acc = along_x ? fma(w, field_diff(sm.n[ty + cy + m][tx + cx + l], sm.n[ty + cy + m][tx + cx - l]), acc)
-                                  : fma(w, field_diff(sm.n[ty + cy + l][tx + cx + m], sm.n[ty + cy - l][tx + cx + m]), acc);
+                for (int m = -3; m <= 3; ++m) {
+                    const int am = m < 0 ? -m : m;
+                    if (glap_c(am, l) != 0.0) {
+                        const float wh = (float)glap_c(am, l);
+                        const float wl = (float)(glap_c(am, l) - (double)(float)glap_c(am, l));
+                        const float2 a = along_x ? sm.n[ty + cy + m][tx + cx + l] : sm.n[ty + cy + l][tx + cx + m];
+                        const float2 b = along_x ? sm.n[ty + cy + m][tx + cx - l] : sm.n[ty + cy - l][tx + cx + m];
+                        const f2 dh = two_sum(a.x, -b.x);
+                        const float dl = dh.lo + (a.y - b.y);
+                        const float p = wh * dh.hi;
+                        const float e = fmaf(wh, dh.hi, -p);
+                        const float tl = fmaf(wh, dl, fmaf(wl, dh.hi, e));
+                        const f2 t2 = two_sum(sum.hi, p);
+                        sum = f2{t2.hi, t2.lo + (sum.lo + tl)};
+                    }
                 }
-            }
+            acc = sum.hi + sum.lo;
+        } else {
+#pragma unroll
+            for (int l = 1; l <= 3; ++l)
+#pragma unroll
+                for (int m = -3; m <= 3; ++m) {
+                    const int am = m < 0 ? -m : m;
+                    if (glap_c(am, l) != 0.0) {
+                        const real w = real(glap_c(am, l));
+                        acc = along_x ? fma(w, field_diff(sm.n[ty + cy + m][tx + cx + l], sm.n[ty + cy + m][tx + cx - l]), acc)
+                                      : fma(w, field_diff(sm.n[ty + cy + l][tx + cx + m], sm.n[ty + cy - l][tx + cx + m]), acc);
+                    }
+                }
+        }
         return acc;
     };
     // With c the stage's coefficient of dt L (Eq. rk3), the node update below
-    // needs per node G = c F, E_q = (c/tau) n g_q(u_x, T) and g_q(u_y, T).
+    // needs per node G = c F, E_q = (c/tau) n g_q(u_x, T) and g_q(u_y, T)
+    // (FP32: n ge_q(u_x, T), n go_q(u_x, T), ge_q(u_y, T), go_q(u_y, T), the
+    // even and odd parts of the factors, in E, Ox, gy, Oy).
     const real sg3 = real(g.sigma) * real(g.inv_ds3);
     const real cit = cc * real(g.inv_tau);
-    real Gx = 0, Gy = 0, E[NQ], gy[NQ];
+    constexpr bool F32 = sizeof(real) == 4;
+    real Gx = 0, Gy = 0, E[NQ], gy[NQ], Ox[NQ], Oy[NQ];
+    real qa = 0, qb = 0, qc = 0;  // FP32: alpha, beta, gamma of the equilibrium's correction (eq_correction)
+    // equilibrium factor sets of the node at (tx_, ty_): x (scaled by n, and
+    // for FP64 by c/tau) into ex, ox and y into ey, oy
+    auto eq_sets = [&](bool x_set, real *a, real *b) {
+        if constexpr (F32) {
+            if (x_set) {
+                eq_factors_split(t, sm.ux[ty][tx], sm.T[ty][tx], a, b);
+                const real nn = sm.n[ty + 3][tx + 4].x;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    a[q] = nn * a[q];
+                    b[q] = nn * b[q];
+                }
+            } else {
+                eq_factors_split(t, sm.uy[ty][tx], sm.T[ty][tx], a, b);
+            }
+        } else {
+            if (x_set) {
+                eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], a);
+                const real cn = cit * field_val(sm.n[ty + 3][tx + 4]);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) a[q] = cn * a[q];
+            } else {
+                eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], a);
+            }
+        }
+    };
     if constexpr (KP == 1) {
         if (active) {
             const real ddx = grad_sum(true), ddy = grad_sum(false);
@@ -406,11 +634,10 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             const real dn = real(g.inv_ds) / nn;
             Gx = cc * fma(ddx, dn, sg3 * ldx);
             Gy = cc * fma(ddy, dn, sg3 * ldy);
-            eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], E);
-            const real cn = cit * nn;
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) E[q] = cn * E[q];
-            eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gy);
+            eq_sets(true, E, Ox);
+            eq_sets(false, gy, Oy);
+            if constexpr (F32)
+                eq_correction(t, E, gy, sm.n[ty + 3][tx + 4], sm.eng[ty][tx], sm.ux[ty][tx], sm.uy[ty][tx], qa, qb, qc);
         }
     } else {
         static_assert(KP == 2 || KP == 4 || KP == 8, "velocity lanes: 1, 2, 4 or 8");
@@ -431,15 +658,35 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             if (lane_ldx) sm.loc[Sm::L_LDX][node] = glap_sum(true);
             if (lane_ldy) sm.loc[Sm::L_LDY][node] = glap_sum(false);
             if (lane_gx) {
-                eq_factors<real>(t, sm.ux[ty][tx], sm.T[ty][tx], E);
-                const real cn = cit * field_val(sm.n[ty + cy][tx + cx]);
+                eq_sets(true, E, Ox);
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) sm.loc[Sm::L_E + q][node] = cn * E[q];
+                for (int q = 0; q < NQ; ++q) {
+                    sm.loc[Sm::L_E + q][node] = E[q];
+                    if constexpr (F32) sm.loc[Sm::L_OX + q][node] = Ox[q];
+                }
             }
             if (lane_gy) {
-                eq_factors<real>(t, sm.uy[ty][tx], sm.T[ty][tx], gy);
+                eq_sets(false, gy, Oy);
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) sm.loc[Sm::L_GY + q][node] = gy[q];
+                for (int q = 0; q < NQ; ++q) {
+                    sm.loc[Sm::L_GY + q][node] = gy[q];
+                    if constexpr (F32) sm.loc[Sm::L_OY + q][node] = Oy[q];
+                }
+            }
+            if constexpr (F32) {
+                // the equilibrium's mass and energy correction, on a lane with
+                // little else to do (KP = 8: lane 6; KP = 4, 2: lane 1), from
+                // the same factors the other lanes store (same operations)
+                if (lane_k == (KP == 8 ? 6 : 1)) {
+                    real ex[NQ], ox[NQ], ey[NQ], oy[NQ];
+                    eq_sets(true, ex, ox);
+                    eq_sets(false, ey, oy);
+                    eq_correction(t, ex, ey, sm.n[ty + 3][tx + 4], sm.eng[ty][tx], sm.ux[ty][tx], sm.uy[ty][tx], qa,
+                                  qb, qc);
+                    sm.loc[Sm::L_CA][node] = qa;
+                    sm.loc[Sm::L_CB][node] = qb;
+                    sm.loc[Sm::L_CC][node] = qc;
+                }
             }
         }
         __syncthreads();
@@ -463,29 +710,48 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     const real cadv = cc * real(g.inv_ds);
     using Sf = FusedSmem<real, TX, TY, KP>;
     constexpr int KF = Sf::KF;
-    // one face value: x face (r, c) or y face (r, c) of velocity k, stored in slot
+    // one face value: x face (r, c) or y face (r, c) of velocity k, stored in
+    // slot (FP32: its WENO correction, from first differences of the pairs)
     auto face = [&](int k, int slot, bool along_x, int r, int c) {
         const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
         if (along_x) {
             if (y0 + r < g.ny && x0 + c <= g.nx) {
                 // face at x = x0 + c: nodes x0+c-3 .. x0+c+2 are columns c+1 .. c+6
                 const real *row = &sm.pop[k][3 + r][0];
-                sm.fx[slot][r][c] =
-                    (k1 > 2) ? face_value<real, LEARNED>(mlp, row[c + 1], row[c + 2], row[c + 3], row[c + 4], row[c + 5])
-                             : face_value<real, LEARNED>(mlp, row[c + 6], row[c + 5], row[c + 4], row[c + 3], row[c + 2]);
+                if constexpr (F32) {
+                    const float *lo = &sm.pl.lo[k][3 + r][0];
+                    auto pd = [&](int a_, int b_) { return pdiff(row[a_], lo[a_], row[b_], lo[b_]); };
+                    sm.fx[slot][r][c] =
+                        (k1 > 2) ? face_corr<LEARNED>(mlp, pd(c + 2, c + 1), pd(c + 3, c + 2), pd(c + 4, c + 3), pd(c + 5, c + 4))
+                                 : face_corr<LEARNED>(mlp, pd(c + 5, c + 6), pd(c + 4, c + 5), pd(c + 3, c + 4), pd(c + 2, c + 3));
+                } else {
+                    sm.fx[slot][r][c] =
+                        (k1 > 2) ? face_value<real, LEARNED>(mlp, row[c + 1], row[c + 2], row[c + 3], row[c + 4], row[c + 5])
+                                 : face_value<real, LEARNED>(mlp, row[c + 6], row[c + 5], row[c + 4], row[c + 3], row[c + 2]);
+                }
             }
         } else if (x0 + c < g.nx && y0 + r <= g.ny) {
             // face at y = y0 + r: rows y0+r-3 .. y0+r+2 are rows r .. r+5
             const int cc4 = 4 + c;
             const real(*P)[HX] = sm.pop[k];
-            sm.fy[slot][r][c] = (k2 > 2) ? face_value<real, LEARNED>(mlp, P[r][cc4], P[r + 1][cc4], P[r + 2][cc4],
-                                                                    P[r + 3][cc4], P[r + 4][cc4])
-                                        : face_value<real, LEARNED>(mlp, P[r + 5][cc4], P[r + 4][cc4], P[r + 3][cc4],
-                                                                    P[r + 2][cc4], P[r + 1][cc4]);
+            if constexpr (F32) {
+                const float(*Lo)[HX] = sm.pl.lo[k];
+                auto pd = [&](int a_, int b_) { return pdiff(P[a_][cc4], Lo[a_][cc4], P[b_][cc4], Lo[b_][cc4]); };
+                sm.fy[slot][r][c] = (k2 > 2) ? face_corr<LEARNED>(mlp, pd(r + 1, r), pd(r + 2, r + 1), pd(r + 3, r + 2), pd(r + 4, r + 3))
+                                             : face_corr<LEARNED>(mlp, pd(r + 4, r + 5), pd(r + 3, r + 4), pd(r + 2, r + 3), pd(r + 1, r + 2));
+            } else {
+                sm.fy[slot][r][c] = (k2 > 2) ? face_value<real, LEARNED>(mlp, P[r][cc4], P[r + 1][cc4], P[r + 2][cc4],
+                                                                        P[r + 3][cc4], P[r + 4][cc4])
+                                            : face_value<real, LEARNED>(mlp, P[r + 5][cc4], P[r + 4][cc4], P[r + 3][cc4],
+                                                                        P[r + 2][cc4], P[r + 1][cc4]);
+            }
         }
     };
-    // node update of velocity k (faces in slot) at tile node (tx_, ty_)
-    auto update = [&](int k, int slot, int tx_, int ty_, real Gx_, real Gy_, real Ek, real gyk) {
+    // node update of velocity k (faces in slot) at tile node (tx_, ty_):
+    // FP64 with Ek = E_q(k1), gyk = g_q(k2); FP32 with Ek = n ge(k1),
+    // oxk = n go(k1), gyk = ge(k2), oyk = go(k2)
+    auto update = [&](int k, int slot, int tx_, int ty_, real Gx_, real Gy_, real Ek, real gyk, real oxk, real oyk,
+                      real qa_, real qb_, real qc_) {
         const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
         const int r = ty_ + 3, c = tx_ + 4;
         real dx = 0, dy = 0;
@@ -495,15 +761,55 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             dy = fma(t.D[k2][q], sm.pop[NQ * k1 + q][r][c], dy);
         }
         const real f = sm.pop[k][r][c];
-        real adv = 0;
-        if (k1 != 2) adv = t.R[k1] * (sm.fx[slot][ty_][tx_ + 1] - sm.fx[slot][ty_][tx_]);
-        if (k2 != 2) adv = fma(t.R[k2], sm.fy[slot][ty_ + 1][tx_] - sm.fy[slot][ty_][tx_], adv);
-        // c L = -c xi.grad f - c F.grad_p f - (c/tau)(f - f^eq) with f^eq = n g g
-        // (Eqs. feq, g_alpha), combined with b f (and a f_n) as in Eq. rk3
-        real v = fma(cf, f, fma(Ek, gyk, -fma(Gx_, dx, fma(Gy_, dy, cadv * adv))));
         const long long o = (long long)(y0 + ty_) * g.pitch + (x0 + tx_);
-        if (ca != real(0)) v = fma(ca, fn[k * g.plane + o], v);
-        out[k * g.plane + o] = v;
+        if constexpr (F32) {
+            // flux difference = difference of the upwind nodes of the two
+            // faces (a first difference of pairs) + difference of corrections
+            const float(*P)[HX] = sm.pop[k];
+            const float(*Lo)[HX] = sm.pl.lo[k];
+            float adv = 0.0f;
+            if (k1 != 2) {
+                const int cu = k1 > 2 ? c : c + 1;
+                adv = t.R[k1] * (pdiff(P[r][cu], Lo[r][cu], P[r][cu - 1], Lo[r][cu - 1]) +
+                                 (sm.fx[slot][ty_][tx_ + 1] - sm.fx[slot][ty_][tx_]));
+            }
+            if (k2 != 2) {
+                const int ru = k2 > 2 ? r : r + 1;
+                adv = fmaf(t.R[k2], pdiff(P[ru][c], Lo[ru][c], P[ru - 1][c], Lo[ru - 1][c]) +
+                                        (sm.fy[slot][ty_ + 1][tx_] - sm.fy[slot][ty_][tx_]), adv);
+            }
+            // f - f^eq with f^eq = n (ge ge + ge go + go (ge + go)) - c: the
+            // exactly symmetric part first, then the parts odd in p_y and in
+            // p_x (each exactly odd after rounding), so that FP32 rounding of
+            // the equilibrium carries no momentum; c (eq_correction) restores
+            // its mass and energy
+            const float fl = Lo[r][c];
+            const float corr =
+                (t.wHe[k1][0] * t.wHe[k2][0]) * fmaf(qc_, t.R2[k1] - t.R2[k2], fmaf(qb_, t.R2[k1] + t.R2[k2], qa_));
+            const float neq = ((((f - Ek * gyk) + fl) - Ek * oyk) - oxk * (gyk + oyk)) + corr;
+            // c L = -c xi.grad f - c F.grad_p f - (c/tau)(f - f^eq), then
+            // out = ca f_n + cb f_s + c L (Eq. rk3) in double-float arithmetic
+            const float inc = -fmaf(cit, neq, fmaf(Gx_, dx, fmaf(Gy_, dy, cadv * adv)));
+            f2 acc = f2_cmul(f2{cb, cb_lo}, f, fl);
+            if (ca != 0.0f) {
+                const f2 an = f2_cmul(f2{ca, ca_lo}, fn[k * g.plane + o], fn[(NK + k) * g.plane + o]);
+                const f2 sh = two_sum(acc.hi, an.hi);
+                acc = f2{sh.hi, sh.lo + (acc.lo + an.lo)};
+            }
+            const f2 si = two_sum(acc.hi, inc);
+            const f2 v = fast_two_sum(si.hi, si.lo + acc.lo);
+            out[k * g.plane + o] = v.hi;
+            out[(NK + k) * g.plane + o] = v.lo;
+        } else {
+            real adv = 0;
+            if (k1 != 2) adv = t.R[k1] * (sm.fx[slot][ty_][tx_ + 1] - sm.fx[slot][ty_][tx_]);
+            if (k2 != 2) adv = fma(t.R[k2], sm.fy[slot][ty_ + 1][tx_] - sm.fy[slot][ty_][tx_], adv);
+            // c L = -c xi.grad f - c F.grad_p f - (c/tau)(f - f^eq) with f^eq = n g g
+            // (Eqs. feq, g_alpha), combined with b f (and a f_n) as in Eq. rk3
+            real v = fma(cf, f, fma(Ek, gyk, -fma(Gx_, dx, fma(Gy_, dy, cadv * adv))));
+            if (ca != real(0)) v = fma(ca, fn[k * g.plane + o], v);
+            out[k * g.plane + o] = v;
+        }
     };
     for (int kb = 0; kb < NK; kb += KF) {
         __syncthreads();  // loc ready / the previous velocities' faces are consumed
@@ -526,15 +832,19 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                     const int r = f / NSX, cs = (f - r * NSX) * SX;
                     // face at x = x0 + c reads columns c+1 .. c+5 (xi_x > 0) or c+6 .. c+2
                     const real *row = &sm.pop[k][3 + r][0];
-                    if (k / NQ > 2) weno5_strip<SX>(row + cs + 1, 1, &sm.fx[k][r][cs], 1);
-                    else weno5_strip<SX>(row + cs + SX + 5, -1, &sm.fx[k][r][cs + SX - 1], -1);
+                    const real *rlo = &sm.pl.lo[k][3 + r][0];
+                    if (k / NQ > 2) weno5_strip_c<SX>(row + cs + 1, rlo + cs + 1, 1, &sm.fx[k][r][cs], 1);
+                    else weno5_strip_c<SX>(row + cs + SX + 5, rlo + cs + SX + 5, -1, &sm.fx[k][r][cs + SX - 1], -1);
                 } else {
                     const int e2 = e - 20 * nsx, ky = e2 / nsy, f = e2 - ky * nsy, q = ky & 3;
                     const int k = (ky >> 2) * NQ + (q < 2 ? q : q + 1);
                     const int rs = (f / TX) * SY, c = f - (f / TX) * TX;
                     // face at y = y0 + r reads rows r .. r+4 (xi_y > 0) or r+5 .. r+1
-                    if (k % NQ > 2) weno5_strip<SY>(&sm.pop[k][rs][4 + c], HX, &sm.fy[k][rs][c], TX);
-                    else weno5_strip<SY>(&sm.pop[k][rs + SY + 4][4 + c], -HX, &sm.fy[k][rs + SY - 1][c], -TX);
+                    if (k % NQ > 2)
+                        weno5_strip_c<SY>(&sm.pop[k][rs][4 + c], &sm.pl.lo[k][rs][4 + c], HX, &sm.fy[k][rs][c], TX);
+                    else
+                        weno5_strip_c<SY>(&sm.pop[k][rs + SY + 4][4 + c], &sm.pl.lo[k][rs + SY + 4][4 + c], -HX,
+                                          &sm.fy[k][rs + SY - 1][c], -TX);
                 }
             }
             // (faces outside the grid are computed from staged values and never read)
@@ -594,22 +904,41 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 const int tx_ = nd % TX, ty_ = nd / TX;
                 if (x0 + tx_ >= g.nx || y0 + ty_ >= g.ny) continue;
                 const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
+                real oxk = 0, oyk = 0, qa_ = 0, qb_ = 0, qc_ = 0;
+                if constexpr (F32) {
+                    oxk = sm.loc[Sf::L_OX + k1][nd];
+                    oyk = sm.loc[Sf::L_OY + k2][nd];
+                    qa_ = sm.loc[Sf::L_CA][nd];
+                    qb_ = sm.loc[Sf::L_CB][nd];
+                    qc_ = sm.loc[Sf::L_CC][nd];
+                }
                 update(k, k, tx_, ty_, sm.loc[Sf::L_G][nd], sm.loc[Sf::L_G + 1][nd], sm.loc[Sf::L_E + k1][nd],
-                       sm.loc[Sf::L_GY + k2][nd]);
+                       sm.loc[Sf::L_GY + k2][nd], oxk, oyk, qa_, qb_, qc_);
             }
         } else {
             const int k = kb + lane_k;
             if (active && k < NK) {
                 const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
-                real Ek, gyk;
+                real Ek, gyk, oxk = 0, oyk = 0, qa_ = qa, qb_ = qb, qc_ = qc;
                 if constexpr (KP > 1) {
                     Ek = sm.loc[Sf::L_E + k1][node];
                     gyk = sm.loc[Sf::L_GY + k2][node];
+                    if constexpr (F32) {
+                        oxk = sm.loc[Sf::L_OX + k1][node];
+                        oyk = sm.loc[Sf::L_OY + k2][node];
+                        qa_ = sm.loc[Sf::L_CA][node];
+                        qb_ = sm.loc[Sf::L_CB][node];
+                        qc_ = sm.loc[Sf::L_CC][node];
+                    }
                 } else {
                     Ek = sel5(E, k1);
                     gyk = sel5(gy, k2);
+                    if constexpr (F32) {
+                        oxk = sel5(Ox, k1);
+                        oyk = sel5(Oy, k2);
+                    }
                 }
-                update(k, lane_k, tx, ty, Gx, Gy, Ek, gyk);
+                update(k, lane_k, tx, ty, Gx, Gy, Ek, gyk, oxk, oyk, qa_, qb_, qc_);
             }
         }
     }
@@ -647,10 +976,11 @@ __global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT,
                                   fused_min_ctas(fused_smem_bytes<real, TX, TY, KP, LEARNED>(),
                                                  FusedSmem<real, TX, TY, KP>::NT, LEARNED))
 k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
-        const __grid_constant__ Geo g, const __grid_constant__ Tab<real> t, real ca, real cb, real cc,
-        const float *__restrict__ mlp)
+        const __grid_constant__ Geo g, const __grid_constant__ Tab<real> t, real ca, real cb, real cc, real ca_lo,
+        real cb_lo, const float *__restrict__ mlp, const __grid_constant__ TmaArg tma)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // 128-byte aligned: the TMA copy of phase 1 lands at offset 0
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<FusedSmem<real, TX, TY, KP> *>(smem_raw);
     float *mlp_sm = nullptr;
     if constexpr (LEARNED) {
@@ -659,7 +989,7 @@ k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict_
         // made visible by the first barrier inside stage_tile
     }
     stage_tile<real, TX, TY, KP, LEARNED>(sm, fs, fn, out, status, g, t, blockIdx.x * TX, blockIdx.y * TY, ca, cb, cc,
-                                          mlp_sm);
+                                          ca_lo, cb_lo, mlp_sm, tma.on ? &tma.map : nullptr);
 }
 
 // Batch of independent runs (uneven grid sizes, own parameters): a
@@ -682,14 +1012,18 @@ static_assert(sizeof(BatchRun<float>) % 16 == 0, "BatchRun<float> must be a whol
 
 template <typename real, int TX, int TY, int KP>
 __global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT,
-                                  // at most two: more would spill the per-item state
-                                  fused_min_ctas(sizeof(FusedSmem<real, TX, TY, KP>) + sizeof(BatchRun<real>),
-                                                 FusedSmem<real, TX, TY, KP>::NT) > 1 ? 2 : 1)
+                                  // FP64: at most two (more would spill the per-item
+                                  // state); FP32: as many as fit, like the single grid
+                                  sizeof(real) == 4
+                                      ? fused_min_ctas(sizeof(FusedSmem<real, TX, TY, KP>) + sizeof(BatchRun<real>),
+                                                       FusedSmem<real, TX, TY, KP>::NT)
+                                      : (fused_min_ctas(sizeof(FusedSmem<real, TX, TY, KP>) + sizeof(BatchRun<real>),
+                                                        FusedSmem<real, TX, TY, KP>::NT) > 1 ? 2 : 1))
 k_fused_batch(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
               const BatchRun<real> *__restrict__ runs, const int *__restrict__ tile_start, int nruns, int total,
-              real ca, real cb, real ccoef)
+              real ca, real cb, real ccoef, real ca_lo, real cb_lo)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<FusedSmem<real, TX, TY, KP> *>(smem_raw);
     __shared__ __align__(16) BatchRun<real> run;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
@@ -709,7 +1043,7 @@ k_fused_batch(const real *__restrict__ fs, const real *fn, real *out, int *__res
         const int lt = item - __ldg(tile_start + lo);
         const int x0 = (lt % run.ntx) * TX, y0 = (lt / run.ntx) * TY;
         stage_tile<real, TX, TY, KP>(sm, fs + run.off, fn + run.off, out + run.off, status + lo, run.g, run.t, x0, y0,
-                                     ca, cb, ccoef * (real)run.g.dt);
+                                     ca, cb, ccoef * (real)run.g.dt, ca_lo, cb_lo);
         __syncthreads();  // the next item overwrites the shared staging
     }
 }
@@ -727,11 +1061,17 @@ cudaError_t fused_prepare_one()
 
 template <typename real, int TX, int TY, int KP, bool LEARNED = false>
 cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *status, const Geo &g,
-                             const Tab<real> &t, StageCoef c, const float *mlp, cudaStream_t s)
+                             const Tab<real> &t, StageCoef c, const float *mlp, const TmaMap *tmap, cudaStream_t s)
 {
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
+    TmaArg tma{};
+    if (tmap) {
+        tma.map = *tmap;
+        tma.on = 1;
+    }
     k_fused<real, TX, TY, KP, LEARNED><<<grid, FusedSmem<real, TX, TY, KP>::NT, fused_smem_bytes<real, TX, TY, KP, LEARNED>(), s>>>(
-        fs, fn, out, status, g, t, (real)c.ca, (real)c.cb, (real)c.cc, mlp);
+        fs, fn, out, status, g, t, (real)c.ca, (real)c.cb, (real)c.cc, (real)(c.ca - (double)(real)c.ca),
+        (real)(c.cb - (double)(real)c.cb), mlp, tma);
     return cudaGetLastError();
 }
 
@@ -754,17 +1094,7 @@ cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, in
     if (grid < 1) return cudaSuccess;
     k_fused_batch<real, TX, TY, KP><<<grid, FusedSmem<real, TX, TY, KP>::NT, sizeof(FusedSmem<real, TX, TY, KP>), s>>>(
         fs, fn, out, status, static_cast<const BatchRun<real> *>(runs), tile_start, nruns, total, (real)c.ca,
-        (real)c.cb, (real)c.cc);
-    return cudaGetLastError();
-}
-
-template <typename real, int TX, int TY, int KP>
-cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *status, const Geo &g,
-                             const Tab<real> &t, StageCoef c, cudaStream_t s)
-{
-    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-    k_fused<real, TX, TY, KP><<<grid, FusedSmem<real, TX, TY, KP>::NT, sizeof(FusedSmem<real, TX, TY, KP>), s>>>(
-        fs, fn, out, status, g, t, (real)c.ca, (real)c.cb, (real)c.cc);
+        (real)c.cb, (real)c.cc, (real)(c.ca - (double)(real)c.ca), (real)(c.cb - (double)(real)c.cb));
     return cudaGetLastError();
 }
 
@@ -780,11 +1110,12 @@ cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *sta
     if (!learned && tx == A && ty == B && kp == C) return fused_prepare_one<real, A, B, C>();
 #define OLB_FUSED_PREP_LEARNED(real, A, B, C) \
     if (learned && tx == A && ty == B && kp == C) return fused_prepare_one<real, A, B, C, true>();
-#define OLB_FUSED_LAUNCH_CASE(real, A, B, C) \
-    if (!mlp && tx == A && ty == B && kp == C) return fused_launch_one<real, A, B, C>(fs, fn, out, status, g, t, c, mlp, s);
+#define OLB_FUSED_LAUNCH_CASE(real, A, B, C)           \
+    if (!mlp && tx == A && ty == B && kp == C)          \
+        return fused_launch_one<real, A, B, C>(fs, fn, out, status, g, t, c, mlp, tma, s);
 #define OLB_FUSED_LAUNCH_LEARNED(real, A, B, C)                 \
     if (mlp && tx == A && ty == B && kp == C)                   \
-        return fused_launch_one<real, A, B, C, true>(fs, fn, out, status, g, t, c, mlp, s);
+        return fused_launch_one<real, A, B, C, true>(fs, fn, out, status, g, t, c, mlp, tma, s);
 #define OLB_FUSED_BATCH_CASE(real, A, B, C)                                                                  \
     if (tx == A && ty == B && kp == C)                                                                       \
         return fused_batch_launch_one<real, A, B, C>(fs, fn, out, status, runs, tile_start, nruns, total, c, s);
@@ -797,7 +1128,7 @@ cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *sta
     }                                                                                                         \
     cudaError_t launch_fused(const real *fs, const real *fn, real *out, int *status, const Geo &g,            \
                              const Tab<real> &t, StageCoef c, int tx, int ty, int kp, const float *mlp,       \
-                             cudaStream_t s)                                                                  \
+                             const TmaMap *tma, cudaStream_t s)                                               \
     {                                                                                                         \
         OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_LAUNCH_CASE)                                                    \
         OLB_FUSED_LEARNED_CASES(real, OLB_FUSED_LAUNCH_LEARNED)                                               \

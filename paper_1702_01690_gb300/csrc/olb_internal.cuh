@@ -1,10 +1,16 @@
 // olb_internal.cuh -- types shared by the library's translation units.
 //
 // Device data layout (all arrays owned by the context):
-//   populations  real f[25][ny][pitch]   kappa = 5*k1 + k2 (x-major velocity
-//                index), pitch = nx rounded up to 32 elements so every row
-//                starts on a 128/256-byte boundary
-//   status       int                     bit 0: invalid moment seen
+//   populations  FP64: double f[25][ny][pitch]   kappa = 5*k1 + k2 (x-major
+//                velocity index), pitch = nx rounded up to 32 elements so
+//                every row starts on a 128/256-byte boundary
+//                FP32: float f[2][25][ny][pitch], the value of population
+//                kappa held as the unevaluated sum hi + lo of plane kappa
+//                (hi, the value rounded to FP32) and plane 25 + kappa (lo,
+//                the remainder rounded to FP32): compensated storage, so that
+//                an RK increment far below FP32 resolution of f survives
+//   status       int                     bit 0: invalid moment seen; bit 1: a
+//                                        bounded wait for a TMA copy ran out
 // The stage kernel keeps moments, force and wall densities of its tile in
 // shared memory; no other global scratch is needed.
 #pragma once
@@ -18,6 +24,14 @@ namespace olb {
 
 constexpr int NQ = 5;   // Gauss-Hermite points per axis (Table trots)
 constexpr int NK = 25;  // velocities
+
+// Planes of one population buffer: 25 in FP64; 50 in FP32 (hi planes, then
+// the lo planes of the compensated storage).
+template <typename real>
+constexpr int pop_planes()
+{
+    return sizeof(real) == 8 ? NK : 2 * NK;
+}
 
 // Geometry and physical parameters, passed by value to every kernel.
 struct Geo {
@@ -35,6 +49,7 @@ template <typename real>
 struct Tab {
     real R[NQ];          // roots of He_5, ascending
     real R2[NQ];         // R^2
+    real R2lo[NQ];       // R^2 - R2 (the remainder of R^2 in this precision; 0 in FP64)
     real D[NQ][NQ];      // (d_p f)_k = sum_k' D[k][k'] f_k'   (Eq. derf)
     real wHe[NQ][NQ];    // w_k He_l(p_k), l = 0..4            (Eq. g_alpha)
     real geqw[2][NK];    // g_{k1}(0, Tw) g_{k2}(uw, Tw) per wall
@@ -57,6 +72,22 @@ int validate_params(const ::olb_params *p);
 void set_sides(Geo *g, const ::olb_params *p);
 int cuda_status(cudaError_t e);
 
+// A TMA tensor map (CUtensorMap, 128 bytes, 64-byte aligned) over one
+// population buffer as a 3-D tensor [planes][ny][nx] with row stride pitch,
+// box (TX + 8) x (TY + 6) x planes: the staged region of a tile in one copy.
+struct alignas(64) TmaMap {
+    unsigned char bytes[128];
+};
+// Kernel argument: the map and whether to use it (tiles whose staged region
+// lies inside the grid are loaded with one TMA copy when on != 0).
+struct alignas(64) TmaArg {
+    TmaMap map;
+    int on;
+};
+// Encode the map of buffer `base` for tile shape tx x ty (olb_api.cu); false
+// if the shape's rows are not a multiple of 16 bytes or the driver refuses.
+bool tma_encode(TmaMap *out, const void *base, bool fp64, const Geo &g, int tx, int ty);
+
 // RK-3 stage coefficients: out = ca f^n + cb f_s + cc L[f_s] (Eq. rk3).
 struct StageCoef {
     double ca, cb, cc;
@@ -68,21 +99,27 @@ struct StageCoef {
     cudaError_t prepare_fused(real *, int tx, int ty, int kp, bool learned);                           \
     cudaError_t launch_fused(const real *fs, const real *fn, real *out, int *status, const Geo &g,     \
                              const Tab<real> &t, StageCoef c, int tx, int ty, int kp,                  \
-                             const float *mlp, cudaStream_t s);                                        \
+                             const float *mlp, const TmaMap *tma, cudaStream_t s);                     \
     cudaError_t launch_fused_batch(const real *fs, const real *fn, real *out, int *status,             \
                                    const void *runs, const int *tile_start, int nruns, int total,      \
                                    StageCoef c, int tx, int ty, int kp, cudaStream_t s);               \
     size_t batch_run_bytes(real *);                                                                    \
     void batch_run_fill(real *, void *dst, const Geo &g, const Tab<real> &t, long long off, int ntx);  \
     cudaError_t launch_init(real *f, const double *n, const double *ux, const double *uy,              \
-                            const double *T, const Geo &g, const Tab<real> &t, cudaStream_t s);         \
+                            const double *T, const Geo &g, const Tab<double> &t, cudaStream_t s);       \
     cudaError_t launch_moments_out(const real *f, double *n, double *ux, double *uy, double *T,        \
-                                   const Geo &g, const Tab<real> &t, cudaStream_t s);                   \
+                                   const Geo &g, const Tab<double> &t, cudaStream_t s);                 \
     cudaError_t launch_to_f64(const real *f, double *dst, const Geo &g, cudaStream_t s);               \
-    cudaError_t launch_from_f64(real *f, const double *src, const Geo &g, cudaStream_t s);
+    cudaError_t launch_from_f64(real *f, const double *src, const Geo &g, cudaStream_t s);             \
+    cudaError_t launch_totals(const real *f, double *partial, double *out, const Geo &g,               \
+                              const Tab<double> &t, cudaStream_t s);
 
 OLB_DECLARE_LAUNCHERS(double)
 OLB_DECLARE_LAUNCHERS(float)
+
+// Global sums (olb_totals): fixed grid of the first reduction pass, whose
+// per-block partial sums (4 each) the second pass adds in a fixed order.
+constexpr int TOTALS_BLOCKS = 1024, TOTALS_THREADS = 256;
 
 // Stage-kernel shapes compiled for both precisions: TX x TY nodes per CTA
 // and KP velocities advanced at once.

@@ -212,6 +212,27 @@ __device__ __forceinline__ void eq_factors(const Tab<real> &t, real u, real T, r
         g[k] = fma(t.wHe[k][4], c4, fma(t.wHe[k][3], c3, fma(t.wHe[k][2], c2, fma(t.wHe[k][1], c1, t.wHe[k][0]))));
 }
 
+// The same factors split by Hermite order parity: ge_k from the even orders
+// l = 0, 2, 4 and go_k from the odd ones l = 1, 3 (g_k = ge_k + go_k).  The
+// tables give w_k He_l(p_k) exactly even or odd under p_k -> -p_k
+// (k -> 4 - k), and ge, go are formed by the same operations on those values,
+// so ge_{4-k} = ge_k and go_{4-k} = -go_k hold exactly, after rounding: a sum
+// over p of p ge (the momentum of the symmetric part) is exactly zero.
+__device__ __forceinline__ void eq_factors_split(const Tab<float> &t, float u, float2 T, float ge[NQ], float go[NQ])
+{
+    // T - 1 from the pair T = hi + lo (hi - 1 is exact for 1/2 <= hi <= 2)
+    const float th = (T.x - 1.0f) + T.y;
+    const float u2 = u * u;
+    const float c2 = 0.5f * (u2 + th);
+    const float c3 = u * fmaf(u2, 1.0f / 6.0f, 0.5f * th);
+    const float c4 = fmaf(u2 * u2, 1.0f / 24.0f, fmaf(0.25f * th, u2, 0.125f * th * th));
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        ge[k] = fmaf(t.wHe[k][4], c4, fmaf(t.wHe[k][2], c2, t.wHe[k][0]));
+        go[k] = fmaf(t.wHe[k][3], c3, t.wHe[k][1] * u);
+    }
+}
+
 // Kahan-compensated accumulation (FP32 variant).
 struct Kahan {
     float s, c;
@@ -279,15 +300,144 @@ __device__ __forceinline__ f2 f2_of(double v)
     return {hi, __double2float_rn(v - (double)hi)};
 }
 
-// Moments of the 25 populations at one node in FP64: n, jx, jy, e.
+// ---------------------------------------------------------------- compensated FP32 storage
+// The FP32 variant stores every population as a pair hi + lo of floats (hi
+// the value rounded to FP32, lo the remainder).  A stage increment dt L is far
+// below the FP32 resolution of f on fine grids (1e-7 .. 1e-5 of f), so plain
+// FP32 storage would round most of it away; the pair keeps it.  The arithmetic
+// stays FP32: first differences of neighbouring pairs,
+// (h1 - h0) + (l1 - l0), are accurate to FP32 rounding of the difference
+// itself (h1 - h0 is exact for neighbouring values of the same sign within a
+// factor 2, Sterbenz), so fluxes, whose differences are all that the
+// advection sees, keep their relative accuracy; the RK-3 combination is done
+// in double-float arithmetic.
+__device__ __forceinline__ float pdiff(float h1, float l1, float h0, float l0) { return (h1 - h0) + (l1 - l0); }
+
+// a + x for a pair a and a float x (|x| anything), renormalised.
+__device__ __forceinline__ f2 f2_add_f(f2 a, float x)
+{
+    const f2 s = two_sum(a.hi, x);
+    return fast_two_sum(s.hi, s.lo + a.lo);
+}
+
+// c a for a double-float constant c and a pair a (both parts of c a formed
+// with exact products where it matters): unnormalised hi + lo.
+__device__ __forceinline__ f2 f2_cmul(f2 c, float ah, float al)
+{
+    const float p = c.hi * ah;
+    const float e = fmaf(c.hi, ah, -p);
+    return {p, fmaf(c.hi, al, fmaf(c.lo, ah, e))};
+}
+
+// Sum of a row of five pairs as a double-float value: TwoSum of the hi parts,
+// their rounding errors and the lo parts gathered in one float.
+__device__ __forceinline__ f2 pair_sum5(const float h[NQ], const float l[NQ])
+{
+    float s = h[0], e = l[0];
+#pragma unroll
+    for (int k = 1; k < NQ; ++k) {
+        const f2 t = two_sum(s, h[k]);
+        s = t.hi;
+        e += t.lo + l[k];
+    }
+    return fast_two_sum(s, e);
+}
+
+// Compensated FP32: the face value v2 + c of the upwind-ordered stencil is
+// kept as v2 (a stored pair) and the correction c = sum_q wbar_q (Fhat^q - v2)
+// of Eq. weno5_flux, which depends on the first differences only; the stage
+// kernel stores c and takes v2 from the populations.
+__device__ __forceinline__ float weno5_corr(float d01, float d12, float d23, float d34)
+{
+    const float q12 = d12 * d12, q23 = d23 * d23;
+    return weno5_core(d01, d12, d23, d34, q23, 2.5f * q12, 2.5f * q23, 0.0f);
+}
+
+// weno5_strip for pairs: the stencil of face j is (ph, pl)[(j + m) step],
+// m = 0..4, the corrections go to out[j ostep]; the first differences of the
+// pairs are carried from face to face.
+template <int S>
+__device__ __forceinline__ void weno5_strip_c(const float *ph, const float *pl, int step, float *out, int ostep)
+{
+    float d01 = pdiff(ph[step], pl[step], ph[0], pl[0]);
+    float d12 = pdiff(ph[2 * step], pl[2 * step], ph[step], pl[step]);
+    float d23 = pdiff(ph[3 * step], pl[3 * step], ph[2 * step], pl[2 * step]);
+    float h12 = 2.5f * (d12 * d12);
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        const float d34 = pdiff(ph[(j + 4) * step], pl[(j + 4) * step], ph[(j + 3) * step], pl[(j + 3) * step]);
+        const float q23 = d23 * d23, h23 = 2.5f * q23;
+        out[j * ostep] = weno5_core(d01, d12, d23, d34, q23, h12, h23, 0.0f);
+        d01 = d12;
+        d12 = d23;
+        d23 = d34;
+        h12 = h23;
+    }
+}
+
+// FP32: the symmetric part s_kappa = Ex[k1] gy[k2] of the equilibrium, as
+// the stage kernel rounds it (Ex = n ge(u_x), gy = ge(u_y), eq_factors_split),
+// carries the node's mass n and energy e = sum |p|^2 f only to FP32 rounding
+// (~1e-7 n); relaxing towards it would create or destroy mass and energy at
+// that rate every stage.  eq_correction returns alpha, beta of the correction
+// c_kappa = W_k1 W_k2 (alpha + beta |p_kappa|^2 + gamma (p_x^2 - p_y^2)),
+// symmetric in p (no momentum), with sum_kappa c = sum s - n,
+// sum |p|^2 c = sum |p|^2 s - e and sum (p_x^2 - p_y^2) c equal to the
+// defect of that moment, from the Gauss-Hermite moments sum W W = 1,
+// sum W W |p|^2 = 2, sum W W |p|^4 = 8: alpha + 2 beta = D_m,
+// 2 alpha + 8 beta = D_e.  The sums of the 25 rounded
+// products are exact (TwoSum); rows and columns 3, 4 equal rows and columns
+// 1, 0 (ge is exactly even), and R^2 of the middle root is 0.
+__device__ __forceinline__ f2 exact_sum5(float a0, float a1, float a2, float a3, float a4)
+{
+    float s = a0, e = 0.0f;
+    const float a[4] = {a1, a2, a3, a4};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const f2 t = two_sum(s, a[k]);
+        s = t.hi;
+        e += t.lo;
+    }
+    return fast_two_sum(s, e);
+}
+__device__ __forceinline__ void eq_correction(const Tab<float> &t, const float Ex[NQ], const float gy[NQ], float2 n,
+                                              float2 e, float ux, float uy, float &alpha, float &beta, float &gamma)
+{
+    float P[NQ][NQ];
+#pragma unroll
+    for (int k1 = 0; k1 < NQ; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < NQ; ++k2) P[k1][k2] = Ex[k1] * gy[k2];
+    const f2 r0 = exact_sum5(P[0][0], P[0][1], P[0][2], P[0][3], P[0][4]);
+    const f2 r1 = exact_sum5(P[1][0], P[1][1], P[1][2], P[1][3], P[1][4]);
+    const f2 r2 = exact_sum5(P[2][0], P[2][1], P[2][2], P[2][3], P[2][4]);
+    const f2 c0 = exact_sum5(P[0][0], P[1][0], P[2][0], P[3][0], P[4][0]);
+    const f2 c1 = exact_sum5(P[0][1], P[1][1], P[2][1], P[3][1], P[4][1]);
+    const f2 mass = f2_add(f2_scale(f2_add(r0, r1), 2.0f), r2);
+    const f2 R24{t.R2[4], t.R2lo[4]}, R23{t.R2[3], t.R2lo[3]};
+    const f2 s4 = f2_add(r0, c0), s3 = f2_add(r1, c1);
+    const f2 ea = f2_cmul(R24, s4.hi, s4.lo), eb = f2_cmul(R23, s3.hi, s3.lo);
+    const f2 energy = f2_scale(f2_add(fast_two_sum(ea.hi, ea.lo), fast_two_sum(eb.hi, eb.lo)), 2.0f);
+    const f2 dm = f2_add(mass, f2{-n.x, -n.y}), de = f2_add(energy, f2{-e.x, -e.y});
+    const float Dm = dm.hi + dm.lo, De = de.hi + de.lo;
+    beta = 0.25f * fmaf(-2.0f, Dm, De);
+    alpha = fmaf(2.0f, Dm, -0.5f * De);
+    // the anisotropic second moment sum (p_x^2 - p_y^2) s, whose target is
+    // n (u_x^2 - u_y^2), rounds the same way; gamma (p_x^2 - p_y^2) W W
+    // (sum W W (p_x^2 - p_y^2)^2 = 4, orthogonal to the two terms above)
+    // removes that defect too, so that relaxation keeps P_xx - P_yy
+    const f2 a4 = f2_add(r0, f2{-c0.hi, -c0.lo}), a3 = f2_add(r1, f2{-c1.hi, -c1.lo});
+    const f2 xa = f2_cmul(R24, a4.hi, a4.lo), xb = f2_cmul(R23, a3.hi, a3.lo);
+    const f2 an = f2_scale(f2_add(fast_two_sum(xa.hi, xa.lo), fast_two_sum(xb.hi, xb.lo)), 2.0f);
+    const float Da = (an.hi - n.x * (ux * ux - uy * uy)) + an.lo;
+    gamma = 0.25f * Da;
+}
+
+// Moments of the 25 populations at one node in FP64: n, jx, jy, e (FP32
+// storage: hi + lo of each population, summed in FP64; output kernels only).
 template <typename real>
 __device__ __forceinline__ void node_sums(const real *__restrict__ f, long long plane, long long o,
-                                          const Tab<real> &t, double &n, double &jx, double &jy, double &e);
-
-template <>
-__device__ __forceinline__ void node_sums<double>(const double *__restrict__ f, long long plane, long long o,
-                                                  const Tab<double> &t, double &n, double &jx, double &jy,
-                                                  double &e)
+                                          const Tab<double> &t, double &n, double &jx, double &jy, double &e)
 {
     double sx[NQ], sy[NQ];
 #pragma unroll
@@ -297,7 +447,9 @@ __device__ __forceinline__ void node_sums<double>(const double *__restrict__ f, 
         double r = 0.0;
 #pragma unroll
         for (int k2 = 0; k2 < NQ; ++k2) {
-            const double v = __ldg(f + (NQ * k1 + k2) * plane + o);
+            const long long q = (NQ * k1 + k2) * plane + o;
+            double v = (double)__ldg(f + q);
+            if constexpr (sizeof(real) == 4) v += (double)__ldg(f + NK * plane + q);
             r += v;
             sy[k2] += v;
         }
@@ -313,50 +465,44 @@ __device__ __forceinline__ void node_sums<double>(const double *__restrict__ f, 
     }
 }
 
-template <>
-__device__ __forceinline__ void node_sums<float>(const float *__restrict__ f, long long plane, long long o,
-                                                 const Tab<float> &t, double &n, double &jx, double &jy,
-                                                 double &e)
+// Store the FP64 value v of population plane offset q: FP64 as is, FP32 as
+// the pair hi + lo.
+__device__ __forceinline__ void store_pop(double *f, long long, long long q, double v) { f[q] = v; }
+__device__ __forceinline__ void store_pop(float *f, long long plane, long long q, double v)
 {
-    Kahan kn{0.f, 0.f}, kx{0.f, 0.f}, ky{0.f, 0.f}, ke{0.f, 0.f};
-#pragma unroll
-    for (int k1 = 0; k1 < NQ; ++k1)
-#pragma unroll
-        for (int k2 = 0; k2 < NQ; ++k2) {
-            const float v = __ldg(f + (NQ * k1 + k2) * plane + o);
-            kn.add(v);
-            kx.add(t.R[k1] * v);
-            ky.add(t.R[k2] * v);
-            ke.add((t.R2[k1] + t.R2[k2]) * v);
-        }
-    n = kn.value();
-    jx = kx.value();
-    jy = ky.value();
-    e = ke.value();
+    const float hi = __double2float_rn(v);
+    f[q] = hi;
+    f[NK * plane + q] = __double2float_rn(v - (double)hi);
+}
+__device__ __forceinline__ double load_pop(const double *f, long long, long long q) { return f[q]; }
+__device__ __forceinline__ double load_pop(const float *f, long long plane, long long q)
+{
+    return (double)f[q] + (double)f[NK * plane + q];
 }
 
 // ---------------------------------------------------------------- init / output
+// f = f^eq(n, u, T) (Eq. feq), evaluated in FP64 for both storages.
 template <typename real>
 __global__ void k_init(real *__restrict__ f, const double *__restrict__ n, const double *__restrict__ ux,
-                       const double *__restrict__ uy, const double *__restrict__ T, Geo g, Tab<real> t)
+                       const double *__restrict__ uy, const double *__restrict__ T, Geo g, Tab<double> t)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)g.nx * g.ny) return;
     const int j = (int)(idx / g.nx), i = (int)(idx - (long long)j * g.nx);
     const long long o = (long long)j * g.pitch + i;
-    real gx[NQ], gy[NQ];
-    eq_factors<real>(t, (real)ux[idx], (real)T[idx], gx);
-    eq_factors<real>(t, (real)uy[idx], (real)T[idx], gy);
-    const real nn = (real)n[idx];
+    double gx[NQ], gy[NQ];
+    eq_factors<double>(t, ux[idx], T[idx], gx);
+    eq_factors<double>(t, uy[idx], T[idx], gy);
+    const double nn = n[idx];
 #pragma unroll
     for (int k1 = 0; k1 < NQ; ++k1)
 #pragma unroll
-        for (int k2 = 0; k2 < NQ; ++k2) f[(NQ * k1 + k2) * g.plane + o] = nn * gx[k1] * gy[k2];
+        for (int k2 = 0; k2 < NQ; ++k2) store_pop(f, g.plane, (NQ * k1 + k2) * g.plane + o, nn * gx[k1] * gy[k2]);
 }
 
 template <typename real>
 __global__ void k_moments_out(const real *__restrict__ f, double *__restrict__ on, double *__restrict__ oux,
-                              double *__restrict__ ouy, double *__restrict__ oT, Geo g, Tab<real> t)
+                              double *__restrict__ ouy, double *__restrict__ oT, Geo g, Tab<double> t)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long N = (long long)g.nx * g.ny;
@@ -381,7 +527,7 @@ __global__ void k_to_f64(const real *__restrict__ f, double *__restrict__ dst, G
     const int k = (int)(idx / N);
     const long long q = idx - (long long)k * N;
     const int j = (int)(q / g.nx), i = (int)(q - (long long)j * g.nx);
-    dst[idx] = (double)f[k * g.plane + (long long)j * g.pitch + i];
+    dst[idx] = load_pop(f, g.plane, k * g.plane + (long long)j * g.pitch + i);
 }
 
 template <typename real>
@@ -393,7 +539,62 @@ __global__ void k_from_f64(real *__restrict__ f, const double *__restrict__ src,
     const int k = (int)(idx / N);
     const long long q = idx - (long long)k * N;
     const int j = (int)(q / g.nx), i = (int)(q - (long long)j * g.nx);
-    f[k * g.plane + (long long)j * g.pitch + i] = (real)src[idx];
+    store_pop(f, g.plane, k * g.plane + (long long)j * g.pitch + i, src[idx]);
+}
+
+// Global sums in FP64 (olb_totals), pass 1: each of TOTALS_BLOCKS blocks
+// takes the nodes idx = block*threads + thread + m*(blocks*threads), sums the
+// node moments n, n u_x, n u_y, e = sum |p|^2/2 f in FP64 per thread, then
+// over the block in a fixed tree order, and writes 4 partial sums.  Pass 2
+// (one block) adds the partials in a fixed order and scales by ds^2.  The
+// order depends only on the grid size: results are reproducible bit for bit.
+template <typename real>
+__global__ void __launch_bounds__(TOTALS_THREADS) k_totals(const real *__restrict__ f, double *__restrict__ partial,
+                                                           Geo g, Tab<double> t)
+{
+    __shared__ double red[4][TOTALS_THREADS];
+    const long long N = (long long)g.nx * g.ny;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long idx = (long long)blockIdx.x * TOTALS_THREADS + threadIdx.x; idx < N;
+         idx += (long long)TOTALS_BLOCKS * TOTALS_THREADS) {
+        const int j = (int)(idx / g.nx), i = (int)(idx - (long long)j * g.nx);
+        double n, jx, jy, e;
+        node_sums<real>(f, g.plane, (long long)j * g.pitch + i, t, n, jx, jy, e);
+        acc[0] += n;
+        acc[1] += jx;
+        acc[2] += jy;
+        acc[3] += 0.5 * e;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = TOTALS_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) partial[(long long)blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+static __global__ void __launch_bounds__(TOTALS_THREADS) k_totals_final(const double *__restrict__ partial,
+                                                                 double *__restrict__ out, double area)
+{
+    __shared__ double red[4][TOTALS_THREADS];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < TOTALS_BLOCKS; b += TOTALS_THREADS)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += partial[4 * b + q];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = TOTALS_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = red[threadIdx.x][0] * area;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -401,14 +602,14 @@ __global__ void k_from_f64(real *__restrict__ f, const double *__restrict__ src,
 // per precision, defined in olb_fp64.cu / olb_fp32.cu).
 #define OLB_DEFINE_AUX_LAUNCHERS(real)                                                                       \
     cudaError_t launch_init(real *f, const double *n, const double *ux, const double *uy, const double *T,   \
-                            const Geo &g, const Tab<real> &t, cudaStream_t s)                                \
+                            const Geo &g, const Tab<double> &t, cudaStream_t s)                              \
     {                                                                                                        \
         const long long N = (long long)g.nx * g.ny;                                                          \
         k_init<real><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(f, n, ux, uy, T, g, t);                     \
         return cudaGetLastError();                                                                           \
     }                                                                                                        \
     cudaError_t launch_moments_out(const real *f, double *n, double *ux, double *uy, double *T,              \
-                                   const Geo &g, const Tab<real> &t, cudaStream_t s)                         \
+                                   const Geo &g, const Tab<double> &t, cudaStream_t s)                       \
     {                                                                                                        \
         const long long N = (long long)g.nx * g.ny;                                                          \
         k_moments_out<real><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(f, n, ux, uy, T, g, t);              \
@@ -424,6 +625,13 @@ __global__ void k_from_f64(real *__restrict__ f, const double *__restrict__ src,
     {                                                                                                        \
         const long long M = (long long)g.nx * g.ny * NK;                                                     \
         k_from_f64<real><<<(unsigned)((M + 255) / 256), 256, 0, s>>>(f, src, g);                             \
+        return cudaGetLastError();                                                                           \
+    }                                                                                                        \
+    cudaError_t launch_totals(const real *f, double *partial, double *out, const Geo &g,                     \
+                              const Tab<double> &t, cudaStream_t s)                                          \
+    {                                                                                                        \
+        k_totals<real><<<TOTALS_BLOCKS, TOTALS_THREADS, 0, s>>>(f, partial, g, t);                           \
+        k_totals_final<<<1, TOTALS_THREADS, 0, s>>>(partial, out, g.ds * g.ds);                              \
         return cudaGetLastError();                                                                           \
     }
 

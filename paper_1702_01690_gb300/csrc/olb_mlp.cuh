@@ -101,4 +101,35 @@ __device__ __forceinline__ real weno5_learned(const float *__restrict__ th, real
     return fma((real)w[0], G1, fma((real)w[1], G2, fma((real)w[2], G3, v2)));
 }
 
+// The same for the compensated FP32 storage: the correction sum_q w_q G_q (the
+// interface value minus v2) from the stencil's first differences d01 .. d34,
+// which fix the normalised stencil (shift invariant) and the candidates.
+__device__ __forceinline__ float weno5_learned_corr(const float *__restrict__ th, float d01, float d12, float d23,
+                                                   float d34)
+{
+    const float a1 = d12 - d01, b1 = fmaf(3.0f, d12, -d01);
+    const float a2 = d23 - d12, b2 = d12 + d23;
+    const float a3 = d34 - d23, b3 = fmaf(-3.0f, d23, d34);
+    const float s1 = fmaf(13.0f * a1, a1, 3.0f * b1 * b1);
+    const float s2 = fmaf(13.0f * a2, a2, 3.0f * b2 * b2);
+    const float s3 = fmaf(13.0f * a3, a3, 3.0f * b3 * b3);
+    const float smin = fminf(s1, fminf(s2, s3)), smax = fmaxf(s1, fmaxf(s2, s3));
+    const bool zero = (a1 == 0.0f && b1 == 0.0f) || (a2 == 0.0f && b2 == 0.0f) || (a3 == 0.0f && b3 == 0.0f);
+    if (zero || smin >= (float)MLP_GUARD * smax) return weno5_corr(d01, d12, d23, d34);
+    // the stencil relative to v0
+    const float w1 = d01, w2 = w1 + d12, w3 = w2 + d23, w4 = w3 + d34;
+    const float mx = fmaxf(fmaxf(0.0f, w1), fmaxf(fmaxf(w2, w3), w4));
+    const float mn = fminf(fminf(0.0f, w1), fminf(fminf(w2, w3), w4));
+    const float mean = (((w1 + w2) + w3) + w4) * 0.2f;
+    const float ir = 1.0f / (mx - mn);
+    const float x[MLP_IN] = {(0.0f - mean) * ir, (w1 - mean) * ir, (w2 - mean) * ir, (w3 - mean) * ir,
+                             (w4 - mean) * ir};
+    float w[MLP_OUT];
+    mlp_weights(th, x, w);
+    const float G1 = fmaf(5.0f / 6.0f, d12, (-1.0f / 3.0f) * d01);
+    const float G2 = fmaf(1.0f / 3.0f, d23, (1.0f / 6.0f) * d12);
+    const float G3 = fmaf(2.0f / 3.0f, d23, (-1.0f / 6.0f) * d34);
+    return fmaf(w[0], G1, fmaf(w[1], G2, w[2] * G3));
+}
+
 }  // namespace olb

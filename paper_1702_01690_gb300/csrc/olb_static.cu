@@ -113,10 +113,20 @@ extern "C" int olb_step_static(const olb_params *p, void *stream, double *f, int
     int *status = reinterpret_cast<int *>(scratch + 2LL * NK * kMaxNodes);
     cudaStream_t s = (cudaStream_t)stream;
 
-    // shape: 16 x 8 nodes with 2 velocity lanes when that gives every SM two
-    // CTAs, else 8 x 8 nodes with 4 lanes
-    const long long ctas = (long long)((g.nx + 15) / 16) * ((g.ny + 7) / 8);
-    const int tx = ctas >= 2 * 152 ? 16 : 8, ty = 8, kp = ctas >= 2 * 152 ? 2 : 4;
+    // shape, as olb_create picks it for FP64: 8 x 8 nodes with 4 velocity
+    // lanes, or 7 x 8 nodes with 8 lanes when that lowers the most nodes one
+    // SM advances (grids here have at most 256 tiles, a wave or two)
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return OLB_ERR_CUDA;
+    }
+    auto most_nodes = [&](int tx_, int ty_) {
+        const long long tiles = (long long)((g.nx + tx_ - 1) / tx_) * ((g.ny + ty_ - 1) / ty_);
+        return (tiles + sms - 1) / sms * tx_ * ty_;
+    };
+    const bool narrow = most_nodes(7, 8) < most_nodes(8, 8);
+    const int tx = narrow ? 7 : 8, ty = 8, kp = narrow ? 8 : 4;
     cudaError_t e = prepare_fused((double *)nullptr, tx, ty, kp, false);
     // the scratch keeps the previous call's contents: the status word must start at zero
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s);
@@ -126,7 +136,7 @@ extern "C" int olb_step_static(const olb_params *p, void *stream, double *f, int
     double *dst[3] = {f1, f2, f};
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
         for (int st = 0; st < 3 && e == cudaSuccess; ++st)
-            e = launch_fused(src[st], f, dst[st], status, g, tab, coef[st], tx, ty, kp, nullptr, s);
+            e = launch_fused(src[st], f, dst[st], status, g, tab, coef[st], tx, ty, kp, nullptr, nullptr, s);
     int hstatus = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

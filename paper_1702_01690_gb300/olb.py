@@ -30,7 +30,7 @@ MLP_PARAMS = 1347
 SYMBOLS = ("olb_set_allocator", "olb_create", "olb_destroy", "olb_init_fields",
            "olb_init_fields_device", "olb_step", "olb_step_async", "olb_get_status",
            "olb_moments", "olb_moments_device", "olb_get_populations",
-           "olb_set_populations", "olb_status_string", "olb_profile", "olb_set_tile", "olb_get_tile", "olb_step_static",
+           "olb_set_populations", "olb_status_string", "olb_profile", "olb_totals", "olb_step_totals", "olb_set_tile", "olb_get_tile", "olb_step_static",
            "olb_batch_create", "olb_batch_destroy", "olb_batch_init_fields", "olb_batch_step",
            "olb_batch_step_async", "olb_batch_get_status", "olb_batch_moments",
            "olb_batch_get_populations", "olb_batch_set_tile", "olb_batch_get_tile",
@@ -71,6 +71,10 @@ for _n in ("olb_get_populations", "olb_set_populations"):
     getattr(_lib, _n).argtypes = [_VP, _VP]
     getattr(_lib, _n).restype = ctypes.c_int
 _lib.olb_profile.argtypes = [_VP, ctypes.c_int, _VP, _VP]
+_lib.olb_totals.argtypes = [_VP, _VP]
+_lib.olb_totals.restype = ctypes.c_int
+_lib.olb_step_totals.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
+_lib.olb_step_totals.restype = ctypes.c_int
 _lib.olb_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
 _lib.olb_set_tile.restype = ctypes.c_int
 _lib.olb_get_tile.argtypes = [_VP, _VP, _VP, _VP]
@@ -265,6 +269,20 @@ class Context:
         _check(_lib.olb_profile(self._h, int(nsteps), ms.ctypes.data_as(_VP), cnt.ctypes.data_as(_VP)),
                "olb_profile")
         return {"stage_ms": float(ms[0]), "stage_launches": int(cnt[0])}
+
+    def totals(self) -> np.ndarray:
+        """Mass, momentum (x, y) and particle kinetic energy summed over the
+        grid (times ds^2), computed on the GPU in FP64."""
+        out = np.zeros(4)
+        _check(_lib.olb_totals(self._h, out.ctypes.data_as(_VP)), "olb_totals")
+        return out
+
+    def step_totals(self, nsteps: int, every: int) -> np.ndarray:
+        """Advance nsteps steps, recording the four sums of totals() after
+        every `every` steps: array [nsteps // every][4]."""
+        out = np.zeros((max(int(nsteps) // int(every), 0), 4))
+        _check(_lib.olb_step_totals(self._h, int(nsteps), int(every), out.ctypes.data_as(_VP)), "olb_step_totals")
+        return out
 
     def set_tile(self, tx: int, ty: int, kp: int) -> None:
         _check(_lib.olb_set_tile(self._h, int(tx), int(ty), int(kp)), "olb_set_tile")

@@ -7,8 +7,10 @@ with smooth fields the force stencils are ill-conditioned (they cancel to
 O(ds^3) of their terms), so there each field must lie within
 max(1e-11 x magnitude, 10 x the rounding envelope): the spread of two oracle
 runs whose states differ by a few ulp per step (helpers.rounding_envelope).
-FP32 + Kahan: within 1e-5 on n and T against the FP64 oracle; u, a small
-difference of O(1) populations, is reported."""
+FP32 (compensated hi + lo storage): n, u and T within 1e-5 of the FP64
+oracle, relative to each field's magnitude, on the planar wall workload at
+its full size (1024 x 8, 200 steps) and on windows of the Laplace-drop
+workload at its full size (2048^2, 10 steps)."""
 import math
 
 import numpy as np
@@ -20,6 +22,7 @@ from paper_1702_01690_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-11
+FP32_TOL = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -93,13 +96,39 @@ def test_ragged_and_tiny_grids(olb, nx, ny, side_x):
 
 def test_planar_walls_full_grid(olb):
     """Planar-interface workload at its full size (1024 x 8, diffuse walls,
-    the launch configuration the benchmark times) for 20 steps."""
+    the launch configuration of the wall workloads) for 200 steps: the
+    populations and n, T within 1e-11 of the oracle relative to their
+    magnitude; u (which the force creates from rest, a small difference of
+    O(1) populations) within max(1e-11 x |u|max, 10 x the rounding envelope)."""
     p, fl = inputs.planar_walls()
     ctx = olb.create(p)
     ctx.init_fields(*fl)
-    assert ctx.step(20) == 0
-    ratio = check_against_envelope(ctx.moments(), p, fl, 20)
-    assert max(ratio.values()) < 1.0, ratio
+    assert ctx.step(200) == 0
+    env, o = rounding_envelope(p, fl, 200)
+    assert field_rel(ctx.get_populations(), o.get_populations()) < FP64_TOL
+    m, ref = ctx.moments(), o.moments()
+    assert field_rel(m[0], ref[0]) < FP64_TOL
+    assert field_rel(m[3], ref[3]) < FP64_TOL
+    us = max(np.max(np.abs(ref[1])), np.max(np.abs(ref[2])))
+    for k in (1, 2):
+        allowed = max(FP64_TOL * us, 10.0 * float(np.max(env[k])))
+        assert np.max(np.abs(m[k] - ref[k])) < allowed, (k, np.max(np.abs(m[k] - ref[k])), allowed)
+
+
+@pytest.mark.parametrize("V", [0.5, 2.0])
+def test_background_velocity_matches_oracle(olb, V):
+    """Shear wave carried at a background velocity V along x (the Galilean
+    runs of Sec. 6.1: T0 = 0.8, tau = 5e-4, dt = 2e-4) on a 32 x 4 periodic
+    grid, 100 steps: n, u, T within 1e-11 of the oracle (u relative to the
+    largest |u|, here V)."""
+    N = 32
+    ds = 1.0 / N
+    p = inputs.RunParams(nx=N, ny=4, ds=ds, dt=2e-4, tau=5e-4, a=0.0, b=0.0)
+    fl = inputs.shear_wave(N, 4, ds, 1.0, 0.8, 1e-3, V=V)
+    ctx, o = run_pair(olb, p, fl, 100)
+    err = moments_rel(ctx.moments(), o.moments())
+    assert max(err.values()) < FP64_TOL, err
+    assert field_rel(ctx.get_populations(), o.get_populations()) < FP64_TOL
 
 
 def test_graph_replay_matches_single_steps(olb):
@@ -305,18 +334,23 @@ def test_phase_separation_4096_sampled_windows(olb):
 # ------------------------------------------------------------------ FP32 + Kahan
 
 def test_fp32_kahan_shear_wave(olb):
+    """Shear-wave workload (64 x 4, 200 steps) in FP32: n, u, T against the
+    FP64 oracle."""
     p, fl = inputs.shear_64x4()
     ctx, o = run_pair(olb, p, fl, p.steps, precision=olb.FP32_KAHAN)
     err = moments_rel(ctx.moments(), o.moments())
-    assert err["n"] < 1e-5 and err["T"] < 1e-5, err
-    assert err["u"] < 5e-3, err
+    print("fp32 shear vs oracle", err)
+    assert max(err.values()) < FP32_TOL, err
 
 
 def test_fp32_kahan_planar_walls(olb):
-    p, fl = inputs.planar_walls(nx=256, ny=8)
-    ctx, o = run_pair(olb, p, fl, 100, precision=olb.FP32_KAHAN)
+    """Planar wall workload at its full size (1024 x 8, 200 steps) in FP32:
+    n, u, T within 1e-5 of the FP64 oracle."""
+    p, fl = inputs.planar_walls()
+    ctx, o = run_pair(olb, p, fl, 200, precision=olb.FP32_KAHAN)
     err = moments_rel(ctx.moments(), o.moments())
-    assert err["n"] < 1e-5 and err["T"] < 1e-5, err
+    print("fp32 planar vs oracle", err)
+    assert max(err.values()) < FP32_TOL, err
 
 
 def test_planar_workload_long_run_conserves_mass(olb):
@@ -385,20 +419,87 @@ def test_every_tile_shape_gives_identical_results_fp32(olb, side_x):
             assert np.array_equal(f, ref), shape
 
 
-def test_fp32_kahan_fine_grid_laplace(olb):
-    """FP32 + Kahan against the FP64 path on the Laplace drop at 1024^2 (fine
-    grid, where the capillary stencil cancels to O(ds^3) of its terms): n, T
-    within 1e-5.  u, created by the force in these few steps, is limited by
-    the FP32 storage of the populations: one RK increment dt L is ~1e-5 of f
-    and rounds at ~1e-2 of itself; measured 4.5e-3 after 10 steps, bound 1e-2."""
-    p, fl = inputs.laplace(1024, R=0.2, steps=10)
-    a = olb.create(p)
+def test_fp32_kahan_laplace_2048_windows(olb):
+    """Laplace-drop workload at its full size (2048^2 periodic) in FP32, 10
+    steps, against the FP64 oracle on windows across the drop interface and
+    in the bulk: n, u, T within 1e-5 of each field's largest value over the
+    grid (u: the largest |u_x|, |u_y|; far from the drop u is ~0).  (On this
+    grid the capillary stencil cancels ~10^3-fold; the FP32 path sums it in
+    double-float arithmetic.)"""
+    steps = 10
+    p, fl = inputs.laplace(2048, R=0.2, steps=steps)
+    ctx = olb.create(p, olb.FP32_KAHAN)
+    ctx.init_fields(*fl)
+    assert ctx.step(steps) == 0
+    m = ctx.moments()
+    scale = {"n": np.max(np.abs(m[0])), "u": max(np.max(np.abs(m[1])), np.max(np.abs(m[2]))),
+             "T": np.max(np.abs(m[3]))}
+    margin = 10 * steps
+    w = 40 + 2 * margin
+    worst = {"n": 0.0, "u": 0.0, "T": 0.0}
+    for x0, y0 in ((1024 - w // 2, 1024 + 410 - w // 2), (1024 + 300 - w // 2, 1024 + 310 - w // 2), (2048 - 60, 2048 - 60)):
+        wp = inputs.RunParams(**{**p.as_dict(), "nx": w, "ny": w})
+        sub = crop_window(fl, x0, y0, w, w, p.nx, p.ny, True)
+        o = make_oracle(wp, sub)
+        o.step(steps)
+        ref = [a[margin:-margin, margin:-margin] for a in o.moments()]
+        ys = np.arange(y0, y0 + w) % p.ny
+        xs = np.arange(x0, x0 + w) % p.nx
+        got = [a[np.ix_(ys, xs)][margin:-margin, margin:-margin] for a in m]
+        e = {"n": np.max(np.abs(got[0] - ref[0])), "u": max(np.max(np.abs(got[1] - ref[1])), np.max(np.abs(got[2] - ref[2]))),
+             "T": np.max(np.abs(got[3] - ref[3]))}
+        worst = {k: max(worst[k], float(e[k] / scale[k])) for k in worst}
+    print("fp32 laplace 2048 windows vs oracle", worst)
+    assert max(worst.values()) < FP32_TOL, worst
+
+
+# ------------------------------------------------------------------ global sums
+
+def host_totals(p, m):
+    """Mass, momentum and particle energy of moments m = (n, ux, uy, T) summed
+    on the host in FP64 (times ds^2): sum n, n u, n (T + |u|^2 / 2)."""
+    n, ux, uy, T = m
+    return np.array([n.sum(), (n * ux).sum(), (n * uy).sum(), (n * (T + 0.5 * (ux ** 2 + uy ** 2))).sum()]) * p.ds ** 2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_totals_match_oracle_sums(olb, precision):
+    """olb_totals (GPU reduction in FP64) against the oracle's state summed on
+    the host after 10 steps of a noisy moving run between diffuse walls: mass
+    and energy to 1e-12 (FP64) / 1e-6 (FP32, whose state differs from the
+    oracle's at that level), momentum relative to sum n |u| ds^2; repeated calls
+    agree bit for bit."""
+    p = inputs.RunParams(nx=45, ny=19, ds=1.0 / 45, dt=0.2 / 45 / inputs.P_MAX, tau=0.01,
+                         Tw=(0.85, 0.95), uw=(0.01, -0.02), side_x=1)
+    fl = noisy(p, seed=11, amp=0.05, uamp=0.01)
+    ctx, o = run_pair(olb, p, fl, 10, precision)
+    got = ctx.totals()
+    assert np.array_equal(got, ctx.totals())
+    m = o.moments()
+    ref = host_totals(p, m)
+    tol = 1e-12 if precision == 0 else 1e-6
+    assert abs(got[0] - ref[0]) < tol * ref[0]
+    assert abs(got[3] - ref[3]) < tol * ref[3]
+    jscale = (m[0] * np.hypot(m[1], m[2])).sum() * p.ds ** 2
+    assert np.max(np.abs(got[1:3] - ref[1:3])) < tol * jscale
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_step_totals_conserve_mass_between_walls(olb, precision):
+    """olb_step_totals on the planar workload (256 x 8, diffuse walls): the
+    records taken every 10 steps keep the mass to 1e-13 (FP64) / 1e-9 (FP32
+    compensated) of itself (zero net wall flux, Eq. nw), the last record equals
+    olb_totals afterwards, and the stepping equals olb_step bit for bit."""
+    p, fl = inputs.planar_walls(nx=256, ny=8)
+    a = olb.create(p, precision)
     a.init_fields(*fl)
-    a.step(10)
-    b = olb.create(p, olb.FP32_KAHAN)
+    m0 = a.totals()[0]
+    rec = a.step_totals(100, 10)
+    assert rec.shape == (10, 4)
+    assert np.array_equal(rec[-1], a.totals())
+    tol = 1e-13 if precision == 0 else 1e-9
+    assert np.max(np.abs(rec[:, 0] - m0)) < tol * m0, rec[:, 0] - m0
+    b = olb.create(p, precision)
     b.init_fields(*fl)
-    b.step(10)
-    err = moments_rel(b.moments(), a.moments())
-    print("fp32 vs fp64 after 10 steps:", err)
-    assert err["n"] < 1e-5 and err["T"] < 1e-5, err
-    assert err["u"] < 1e-2, err
+    b.step(100)
+    assert np.array_equal(a.get_populations(), b.get_populations())
