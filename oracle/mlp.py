@@ -140,3 +140,18 @@ def network_acts(V):
     min sigma < GUARD max sigma."""
     S = sigmas(V)
     return (S.min(axis=1) > 0) & (S.min(axis=1) < GUARD * S.max(axis=1))
+
+
+def js_face_values(V):
+    """Jiang-Shu WENO-5 interface values of stencils V [S][5] (upwind order):
+    Eq. weno5_omega without epsilon, Table tab:weno where an indicator
+    vanishes (the same reading as orc_weno5, vectorised for many stencils)."""
+    V = np.asarray(V, dtype=np.float64)
+    S = sigmas(V)
+    d = np.array([0.1, 0.6, 0.3])
+    zero = S == 0
+    anyz = zero.any(axis=1)
+    Sn = np.where(zero, 1.0, S)
+    wt = np.where(anyz[:, None], d * zero, d / Sn ** 2)
+    wt = wt / wt.sum(axis=1, keepdims=True)
+    return V[:, 2] + (wt * candidates(V)).sum(axis=1)

@@ -27,6 +27,8 @@ olb_mlp_train.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 from . import inputs
@@ -180,41 +182,36 @@ def train(x, Gn, tn, epochs: int = 40, batch: int = 4096, lr: float = 2e-3, seed
     return theta.cpu().numpy(), hist
 
 
-def js_face_values(V):
-    """Jiang-Shu WENO-5 interface values (Eq. weno5_omega with eps = 0 and
-    Table tab:weno) of stencils V [S][5], for comparisons on the host."""
-    V = np.asarray(V, dtype=np.float64)
-    v0, v1, v2, v3, v4 = V.T
-    s1 = 13 / 12 * (v0 - 2 * v1 + v2) ** 2 + 0.25 * (v0 - 4 * v1 + 3 * v2) ** 2
-    s2 = 13 / 12 * (v1 - 2 * v2 + v3) ** 2 + 0.25 * (v1 - v3) ** 2
-    s3 = 13 / 12 * (v2 - 2 * v3 + v4) ** 2 + 0.25 * (3 * v2 - 4 * v3 + v4) ** 2
-    S = np.stack([s1, s2, s3], axis=1)
-    d = np.array([0.1, 0.6, 0.3])
-    zero = S == 0
-    anyz = zero.any(axis=1)
-    smin = np.where(anyz, 1.0, S.min(axis=1))
-    wt = np.where(anyz[:, None], d * zero, d * (smin[:, None] / np.where(S == 0, 1.0, S)) ** 2)
-    wt = wt / wt.sum(axis=1, keepdims=True)
-    return v2 + (wt * candidate_offsets(V)).sum(axis=1)
+THETA_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weno_mlp_theta.txt")
 
 
-def learned_face_values(theta, V):
-    """Interface values with the network's weights (FP64 evaluation on the
-    host; Jiang-Shu weights where the network does not act)."""
-    V = np.asarray(V, dtype=np.float64)
-    th = np.asarray(theta, dtype=np.float64)
-    W1, b1 = th[:160].reshape(32, 5), th[160:192]
-    W2, b2 = th[192:1216].reshape(32, 32), th[1216:1248]
-    W3, b3 = th[1248:1344].reshape(3, 32), th[1344:1347]
-    r = V.max(axis=1) - V.min(axis=1)
-    rs = np.where(r > 0, r, 1.0)
-    x = (V - V.mean(axis=1, keepdims=True)) / rs[:, None]
-    z = np.tanh(np.tanh(x @ W1.T + b1) @ W2.T + b2) @ W3.T + b3
-    z -= z.max(axis=1, keepdims=True)
-    w = np.exp(z)
-    w /= w.sum(axis=1, keepdims=True)
-    out = V[:, 2] + (w * candidate_offsets(V)).sum(axis=1)
-    js = ~network_acts(V)
-    if js.any():
-        out[js] = js_face_values(V[js])
-    return out
+def save_theta(theta, path: str = THETA_FILE) -> None:
+    """Write the 1347 network parameters as text (9 significant digits, exact
+    for float32)."""
+    th = np.asarray(theta, dtype=np.float32).reshape(-1)
+    assert th.size == 1347
+    np.savetxt(path, th, fmt="%.9e", header="5-32-32-3 WENO-5 weight network, parameters W1 b1 W2 b2 W3 b3")
+
+
+def load_theta(path: str = THETA_FILE) -> np.ndarray:
+    """The parameters written by save_theta (float32)."""
+    th = np.loadtxt(path, dtype=np.float64).astype(np.float32)
+    assert th.size == 1347
+    return th
+
+
+def train_default(epochs: int = 30, seed: int = 0):
+    """Harvest the default training runs and train on all their stencils
+    (GPU); returns (theta, loss history, number of samples)."""
+    V, t, s = harvest(default_sources(), ratio=4, row_stride=16)
+    (x, Gn, tn), _ = normalised_samples(V, t, s)
+    theta, hist = train(x, Gn, tn, epochs=epochs, batch=4096, lr=2e-3, seed=seed)
+    return theta, hist, len(tn)
+
+
+if __name__ == "__main__":
+    # python -m paper_1702_01690_gb300.learned [path]: train the shipped network
+    import sys
+    theta, hist, n = train_default()
+    save_theta(theta, sys.argv[1] if len(sys.argv) > 1 else THETA_FILE)
+    print(f"trained on {n} stencils; loss per epoch {hist.tolist()}")

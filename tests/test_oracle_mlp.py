@@ -86,3 +86,18 @@ def test_learned_weights_shift_and_scale_invariant():
         _, w1 = oracle.weno5_learned(theta, v, return_weights=True)
         _, w2 = oracle.weno5_learned(theta, 4.0 * v - 1.5, return_weights=True)
         np.testing.assert_allclose(w1, w2, rtol=1e-12)
+
+
+def test_vectorised_js_values_equal_the_c_oracle():
+    """mlp.js_face_values (many stencils at once) against orc_weno5, itself
+    pinned by Table tab:weno and exactness on quadratics: random stencils,
+    stencils with one, two or three vanishing indicators."""
+    rng = np.random.default_rng(5)
+    V = list(rng.normal(size=(200, 5)).cumsum(axis=1))
+    V += [np.array([1.0, 1.0, 1.0, 2.0, 4.0]), np.array([0.0, 1.0, 2.0, 3.0, 4.0]),
+          np.array([3.0, 3.0, 3.0, 3.0, 3.0]), np.array([1.0, 2.0, 3.0, 3.0, 3.0]),
+          np.array([5.0, 1.0, 2.0, 3.0, 4.0])]
+    V = np.array(V)
+    ref = np.array([oracle.weno5(v) for v in V])
+    got = mlp.js_face_values(V)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
