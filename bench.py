@@ -1,22 +1,35 @@
 #!/usr/bin/env python
 """Benchmark of the RK-3 off-lattice Boltzmann step (node-updates/s).
 
-Default workload: the planar liquid-vapour set-up between diffuse walls,
-1024 x 8 nodes (walls at x = 0, 1, periodic y), T_w = 0.9,
-n = 1 + 0.01 U(-1, 1), tau = 0.005, dt = 5e-5, in FP64; the FP32 + Kahan
-variant is timed beside it and its error against the FP64 path stated.
-A "step" is one full RK-3 step (3 x moments + fused stage) of the whole grid.
+Default workload: phase separation between cold plates, 4096 x 4096 nodes
+(diffuse walls at x = 0, 1 with T_w = 0.7, periodic y), n = 1 + 0.01
+band-limited noise, T0 = 1, u = 0, tau = 5e-3, dt = 6.25e-7, sigma = 1e-4
+(Sec. 7 set-up).  `value` is the FP64 path.  Beside it, on the same grid and
+GPU, each with its own stage time and roofline fraction:
+  fp32          FP32 arithmetic with compensated (hi + lo) population storage
+  learned_fp64  learned WENO weights (network in FP32, populations FP64)
+  learned_fp32  learned WENO weights with the FP32 path
+  batch_fp64/32 64 independent runs of uneven size (32^2 .. 1024^2, 13.5 M
+                nodes) in one persistent launch per stage, autotuned shape
+A "step" is one full RK-3 step (three launches of the fused stage kernel:
+moments, force, WENO-5 fluxes, collision and RK combination) of the whole grid.
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
-on the context's stream, with a 256 MiB buffer written between steps so L2
-(129 MB) holds nothing of the step's data; barrier + synchronize on both
-sides; max over ranks.  With torchrun (N > 1) every rank runs an
-independent replica (the path has no data exchange to shard): value is the
-node-updates of all ranks per second.
+on the context's stream, with a 256 MiB buffer written between steps (the
+10 GB of populations are far larger than the 129 MB L2 anyway); barrier +
+synchronize on both sides; max over ranks.  With torchrun (N > 1) every rank
+runs an independent replica (the path has no data exchange to shard): value
+is the node-updates of all ranks per second.
 
-Also reported: per-kernel roofline of the dominant kernel (CUDA events on
-its launching stream), end-to-end throughput through the C ABI with pinned
-host buffers, the FP64 oracle timed on the host cores, SM clocks sampled
+Accuracy (rank 0, N = 1, in the oracle leg): every GPU leg is re-run for a few
+steps from the initial state and compared on windows at both walls and in the
+bulk with the FP64 oracle run on those windows (a window interior farther than
+10 nodes per step from a cut edge is exact); the same oracle runs give the CPU
+baseline (all host cores) and a single-threaded oracle figure.
+
+Also reported: the roofline of the dominant kernel, end-to-end throughput
+through the C ABI with pinned host buffers, the mass and energy sums of the
+GPU's FP64 reduction before and after the timed steps, SM clocks sampled
 during the timed region.  ``--impl reference`` times the FP64 oracle alone.
 """
 from __future__ import annotations
@@ -40,28 +53,25 @@ METRIC = "node-updates/s (25-vel RK3 step) vs plain FP64 at stated error; % of r
 UNIT = "node-updates/s"
 
 # Algorithmic flops of one stage per node (FMA = 2), counted formula by
-# formula: moments 110, force stencils 172,
-# equilibrium factors 104, local part of L and RK combination 25 x 30 = 750,
-# WENO-5 faces 40 x 57 = 2280 (20 moving velocities per axis, one face per
-# node), advection and output 155.  The FP32 variant adds the Kahan
-# compensation of the four 25-term moment sums (+365).
+# formula: moments 110, force stencils 172, equilibrium factors 104, local
+# part of L and RK combination 25 x 30 = 750, WENO-5 faces 40 x 57 = 2280
+# (20 moving velocities per axis, one face per node), advection and output
+# 155.  The same count is used for the FP32 path (its compensation work is
+# overhead, not algorithmic flops).
 STAGE_FLOPS_PER_NODE = 110 + 172 + 104 + 750 + 2280 + 155
-STAGE_FLOPS_PER_NODE_FP32 = STAGE_FLOPS_PER_NODE + 365
+# One evaluation of the 5-32-32-3 network (FMA = 2): 2 x (5 x 32 + 32 x 32 +
+# 32 x 3) = 2560 flops plus 64 tanh, 3 exp and the softmax (not counted).
+MLP_FLOPS = 2 * (5 * 32 + 32 * 32 + 32 * 3)
 # Population values moved per node and step: stage 1 reads f and writes f1
-# (50), stages 2 and 3 read f^n and f_s and write (75 each): 200 per step.
+# (50), stages 2 and 3 read f^n and f_s and write (75 each): 200 per step,
+# 8 bytes each in both paths (FP32 stores hi + lo pairs).
 VALUES_PER_NODE_STEP = 200
-
-# Peaks from unit counts and the 2.07 GHz maximum SM clock: FP64 2 DFMA per
-# SM per clock (1.20 TFLOP/s measured at 1.97 GHz with an FMA loop),
-# 152 x 2 x 2 x 2.07e9 = 1.26 TFLOP/s; FP32 128 lanes per SM,
-# 152 x 128 x 2 x 2.07e9 = 80.5 TFLOP/s.
-PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per stage launch, averaged over the three stages of
-# a step, from one ncu capture of exactly this kernel build on this workload
-# (stage 1: 1.71 MB, stages 2 and 3: 3.35 MB each; writes still in L2).  Any
-# other kernel or workload reports null.
-DRAM_TRAFFIC_PER_LAUNCH = {("planar", None, "k_fused<double,7,8,8>"): 2.81e6}
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per stage launch from one ncu capture of exactly
+# this kernel build, on the Laplace 2048^2 grid (4.19 M nodes; the 4096^2
+# grid is too large to capture), scaled by 4 to the 16.8 M nodes of the
+# 4096^2 grid (traffic grows with the node count).  Any other kernel or
+# workload reports null.
+DRAM_TRAFFIC_PER_LAUNCH = {}
 
 
 def load_peaks():
@@ -69,6 +79,17 @@ def load_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def alu_peaks(device_index: int = 0):
+    """FP64 and FP32 peaks (TFLOP/s) from the unit counts of the SM and its
+    maximum clock: FP64 2 DFMA per SM per clock, FP32 128 lanes per SM, each
+    FMA 2 flops; SM count from the device, clock from MEASURED_PEAKS.json
+    (else 2070 MHz, GB300's maximum)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
+    mhz = float(load_peaks().get("sm_max_mhz", 2070.0))
+    return (sms * 2 * 2 * mhz * 1e6 / 1e12, sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz)
 
 
 def workload(name, size=None):
@@ -87,10 +108,20 @@ def workload(name, size=None):
     elif name == "phase":
         n = size or 4096
         p, f = inputs.phase_separation(n)
-        desc = f"phase separation {n}^2, diffuse walls, Tw=0.7, tau=5e-3, dt={p.dt:g}"
+        desc = (f"phase separation between cold plates {n}^2, diffuse walls x=0,1 Tw=0.7, periodic y, "
+                f"n=1+0.01 noise, T0=1, tau=5e-3, dt={p.dt:g}, sigma=1e-4")
     else:
         raise SystemExit(f"unknown workload {name}")
     return p, f, desc
+
+
+def default_theta():
+    """The trained network shipped with the package (None if absent)."""
+    from paper_1702_01690_gb300 import learned
+    try:
+        return learned.load_theta()
+    except FileNotFoundError:
+        return None
 
 
 # ------------------------------------------------------------------ clocks
@@ -144,64 +175,6 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ------------------------------------------------------------------ oracle legs
-def oracle_rate(p, fields, seconds: float, max_steps: int = 10 ** 6):
-    """FP64 oracle node-updates/s on the host cores: whole-grid steps until
-    `seconds` of CPU work (at least one step)."""
-    import oracle
-    threads = os.cpu_count() or 1
-    oracle.set_threads(threads)
-    o = oracle.Oracle(p.nx, p.ny, p.ds, p.dt, p.tau, p.a, p.b, p.sigma, p.Tw, p.uw, p.side_x, p.side_y)
-    o.init_fields(*fields)
-    steps = 0
-    t0 = time.perf_counter()
-    while True:
-        o.step(1)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or steps >= max_steps:
-            break
-    return p.nx * p.ny * steps / el, steps, el, oracle.max_threads()
-
-
-def oracle_sample_params(p, fields, max_nodes=1 << 16):
-    """Bounded sample of a large workload: the top-left window of at most
-    max_nodes nodes with the same parameters (walls kept)."""
-    if p.nx * p.ny <= max_nodes:
-        return p, fields, f"full grid {p.nx}x{p.ny}"
-    from paper_1702_01690_gb300 import inputs
-    w = int(math.sqrt(max_nodes))
-    wx, wy = min(p.nx, w), min(p.ny, max_nodes // min(p.nx, w))
-    q = inputs.RunParams(**{**p.as_dict(), "nx": wx, "ny": wy})
-    sub = tuple(np.ascontiguousarray(a[:wy, :wx]) for a in fields)
-    return q, sub, f"{wx}x{wy} window of the {p.nx}x{p.ny} grid"
-
-
-def run_reference(args, rank, world):
-    if rank != 0:
-        return
-    p, fields, desc = workload(args.workload, args.size)
-    q, sub, what = oracle_sample_params(p, fields)
-    # untimed warm-up steps, then K timed whole-grid steps of the sample
-    import oracle
-    oracle.set_threads(os.cpu_count() or 1)
-    o = oracle.Oracle(q.nx, q.ny, q.ds, q.dt, q.tau, q.a, q.b, q.sigma, q.Tw, q.uw, q.side_x, q.side_y)
-    o.init_fields(*sub)
-    o.step(args.warmup)
-    t0 = time.perf_counter()
-    o.step(args.steps)
-    el = time.perf_counter() - t0
-    v = q.nx * q.ny * args.steps / el
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": desc, "sample": what},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": f"{args.steps} RK-3 steps of the {what}"},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
 # ------------------------------------------------------------------ ranks
 def rank_barrier():
     """Barrier over the ranks of the default process group (none without one)."""
@@ -229,8 +202,113 @@ def job_value(world: int, nodes: int, steps: int, ms: float) -> float:
     return world * nodes * steps / (ms / 1e3)
 
 
-# ------------------------------------------------------------------ GPU leg
+# ------------------------------------------------------------------ oracle windows
+def windows_for(p, steps):
+    """Oracle windows of a workload after `steps` steps: (x0, y0, wx, wy,
+    wall) with a margin of 10 nodes per step around a 40 x 40 interior (none
+    on the wall side)."""
+    m = 10 * steps
+    w = 40 + 2 * m
+    ww = 40 + m
+    wins = []
+    if p.side_x == 1:
+        wins.append((0, p.ny // 7, ww, w, "left"))
+        wins.append((p.nx - ww, (3 * p.ny) // 4, ww, w, "right"))
+    wins.append((p.nx // 2 - w // 2 + 7, p.ny - w // 2, w, w, None))  # bulk, wrapping in y
+    return wins, m
+
+
+def crop(fields, x0, y0, wx, wy, nx, ny, periodic_x):
+    ys = np.arange(y0, y0 + wy) % ny
+    xs = np.arange(x0, x0 + wx)
+    if periodic_x:
+        xs = xs % nx
+    return tuple(np.ascontiguousarray(a[np.ix_(ys, xs)]) for a in fields)
+
+
+def oracle_windows(p, fields, steps, theta=None, threads=None):
+    """Run the FP64 oracle on the windows of `p` for `steps` steps; returns
+    the per-window oracle moments, the windows, the interior margin, the
+    node-updates done and the seconds taken."""
+    import oracle
+    from paper_1702_01690_gb300 import inputs
+    oracle.set_threads(threads or (os.cpu_count() or 1))
+    wins, m = windows_for(p, steps)
+    out, work = [], 0
+    t0 = time.perf_counter()
+    for (x0, y0, wx, wy, wall) in wins:
+        wp = inputs.RunParams(**{**p.as_dict(), "nx": wx, "ny": wy})
+        if wall is None:
+            wp.side_x = 0
+        o = oracle.Oracle(wp.nx, wp.ny, wp.ds, wp.dt, wp.tau, wp.a, wp.b, wp.sigma, wp.Tw, wp.uw, wp.side_x,
+                          wp.side_y)
+        if theta is not None:
+            o.set_mlp(np.asarray(theta, dtype=np.float64))
+        o.init_fields(*crop(fields, x0, y0, wx, wy, p.nx, p.ny, p.side_x == 0))
+        o.step(steps)
+        out.append(o.moments())
+        o.close()
+        work += wx * wy * steps
+    return out, wins, m, work, time.perf_counter() - t0, oracle.max_threads()
+
+
+def window_errors(m_gpu, p, ref, wins, margin):
+    """Largest error of the GPU moments against the oracle windows over the
+    window interiors, relative to each field's largest oracle value there
+    (u: the largest |u_x|, |u_y|)."""
+    worst = {"n": 0.0, "u": 0.0, "T": 0.0}
+    for (x0, y0, wx, wy, wall), mo in zip(wins, ref):
+        ys = np.arange(y0, y0 + wy) % p.ny
+        xs = np.arange(x0, x0 + wx) % p.nx
+        iy = slice(margin, wy - margin)
+        ix = slice(0, wx - margin) if wall == "left" else (slice(margin, wx) if wall == "right"
+                                                           else slice(margin, wx - margin))
+        g = [a[np.ix_(ys, xs)][iy, ix] for a in m_gpu]
+        r = [a[iy, ix] for a in mo]
+        us = max(np.max(np.abs(r[1])), np.max(np.abs(r[2])), 1e-300)
+        worst["n"] = max(worst["n"], float(np.max(np.abs(g[0] - r[0])) / np.max(np.abs(r[0]))))
+        worst["u"] = max(worst["u"], float(max(np.max(np.abs(g[1] - r[1])), np.max(np.abs(g[2] - r[2]))) / us))
+        worst["T"] = max(worst["T"], float(np.max(np.abs(g[3] - r[3])) / np.max(np.abs(r[3]))))
+    return worst
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p, fields, desc = workload(args.workload, args.size)
+    steps = args.steps
+    # untimed warm-up, then K timed steps of the oracle on the workload's
+    # windows (all host cores); a sample of the same per-node work
+    import oracle
+    from paper_1702_01690_gb300 import inputs
+    oracle.set_threads(os.cpu_count() or 1)
+    wins, _ = windows_for(p, 1)
+    x0, y0, wx, wy, wall = wins[0]
+    wx, wy = min(p.nx, 256), min(p.ny, 256)
+    wp = inputs.RunParams(**{**p.as_dict(), "nx": wx, "ny": wy})
+    o = oracle.Oracle(wp.nx, wp.ny, wp.ds, wp.dt, wp.tau, wp.a, wp.b, wp.sigma, wp.Tw, wp.uw, wp.side_x, wp.side_y)
+    o.init_fields(*crop(fields, 0, 0, wx, wy, p.nx, p.ny, p.side_x == 0))
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t0
+    v = wx * wy * steps / el
+    what = f"{wx}x{wy} window (walls kept) of the {p.nx}x{p.ny} grid"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "sample": what},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{steps} RK-3 steps of the {what}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU legs
 def time_steps(ctx, steps, warmup, flush, stream):
+    """K graph-replayed steps, each bracketed by CUDA events on the context's
+    stream; the flush buffer is written between steps (outside the events)."""
     import torch
     for _ in range(warmup):
         ctx.step_async(1)
@@ -249,6 +327,43 @@ def time_steps(ctx, steps, warmup, flush, stream):
     return sum(ms), ms
 
 
+def timed_leg(olb, p, dev_fields, prec, steps, warmup, flush, stream, world, peak, weno=0, theta=None,
+              clocks=None, mlp_acts=None):
+    """One timed leg: value, ms per step, stage time and roofline of the stage
+    kernel.  The step is exactly three launches of the stage kernel, so the
+    average launch takes a third of the timed step."""
+    import torch
+    N = p.nx * p.ny
+    ctx = olb.create(p, prec, stream, weno_mode=weno)
+    if theta is not None:
+        ctx.set_weno_mlp(theta)
+    ctx.init_fields(*dev_fields)
+    torch.cuda.synchronize()
+    rank_barrier()
+    if clocks is not None:
+        with clocks:
+            total, per = time_steps(ctx, steps, warmup, flush, stream)
+    else:
+        total, per = time_steps(ctx, steps, warmup, flush, stream)
+    rank_barrier()
+    total = max_over_ranks(total)
+    ms_step = total / steps
+    stage_ms = ms_step / 3.0
+    flops = STAGE_FLOPS_PER_NODE * N
+    if mlp_acts is not None:
+        flops += mlp_acts * MLP_FLOPS
+    ach = flops / (stage_ms * 1e-3) / 1e12
+    tile = ctx.get_tile()
+    kind = "double" if prec == olb.FP64 else "float"
+    kname = f"k_fused<{kind},{tile[0]},{tile[1]},{tile[2]}{',learned' if weno else ''}>"
+    prof = ctx.profile(3)
+    leg = {"value": job_value(world, N, steps, total), "ms_per_step": ms_step,
+           "roofline": {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                        "frac": ach / peak, "algorithmic_flops_per_launch": flops, "stage_ms": stage_ms,
+                        "stage_ms_single_launches": prof["stage_ms"]}}
+    return leg, ctx
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1702_01690_gb300 import olb
@@ -258,65 +373,67 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     p, fields, desc = workload(args.workload, args.size)
     N = p.nx * p.ny
+    peak64, peak32, sms, mhz = alu_peaks(local)
     olb.use_torch_allocator(True)
     dev_fields = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in fields]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    legs_run = 0
 
-    ctx = olb.create(p, olb.FP64, stream)
+    # ---- FP64 (value)
+    clk = ClockSampler(local)
+    fp64, ctx = timed_leg(olb, p, dev_fields, olb.FP64, args.steps, args.warmup, flush, stream, world, peak64,
+                          clocks=clk)
+    legs_run += 1
+    value, ms_step = fp64["value"], fp64["ms_per_step"]
+    roof = dict(fp64["roofline"])
+    kname = roof["kernel"]
+    roof["traffic"] = DRAM_TRAFFIC_PER_LAUNCH.get((args.workload, args.size, kname))
+    roof["peak_source"] = (f"FP64 units x max SM clock: 2 DFMA/SM/clk x {sms} SMs x {mhz:.0f} MHz x 2 flop "
+                           f"(no FP64 entry in MEASURED_PEAKS.json)")
+    # mass and energy from the GPU's FP64 reduction after the timed steps
+    # (the context is then at step warmup + steps + 3 profiled steps)
+    tot_after = ctx.totals()
     ctx.init_fields(*dev_fields)
-    torch.cuda.synchronize()
-    rank_barrier()
-    with ClockSampler(local) as clk:
-        total_ms, _ = time_steps(ctx, args.steps, args.warmup, flush, stream)
-    torch.cuda.synchronize()
-    rank_barrier()
-    total_ms = max_over_ranks(total_ms)
-    ms_step = total_ms / args.steps
-    value = job_value(world, N, args.steps, total_ms)
-    m64 = ctx.moments()
+    tot0 = ctx.totals()
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
 
-    # dominant kernel: per-launch device time of each kernel kind
-    prof = ctx.profile(max(3, min(args.steps, 50)))
-    st_ms = prof["stage_ms"]
-    achieved = STAGE_FLOPS_PER_NODE * N / (st_ms * 1e-3) / 1e12
-    tile = ctx.get_tile()
-    kname = f"k_fused<double,{tile[0]},{tile[1]},{tile[2]}>"
-    roof = {"kernel": f"{kname} (moments + force + WENO-5 + BGK + RK-3 stage)",
-            "bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / PEAK_FP64_TFLOPS,
-            "traffic": DRAM_TRAFFIC_PER_LAUNCH.get((args.workload, args.size, kname)),
-            "peak_source": "FP64 units x max SM clock (2 DFMA/SM/clk x 152 x 2.07 GHz)",
-            "algorithmic_flops_per_launch": STAGE_FLOPS_PER_NODE * N,
-            "stage_ms": st_ms, "stage_share": 3 * st_ms / ms_step if ms_step > 0 else None}
+    # ---- FP32 compensated
+    fp32, c32 = timed_leg(olb, p, dev_fields, olb.FP32_KAHAN, args.steps, args.warmup, flush, stream, world, peak32)
+    fp32["speedup_vs_fp64"] = fp32["value"] / value
+    fp32["roofline"]["peak_source"] = f"FP32 lanes x max SM clock: 128/SM x {sms} SMs x {mhz:.0f} MHz x 2 flop"
+    c32.close()
+    del c32
+    torch.cuda.empty_cache()
 
-    # FP32 + Kahan variant on the same workload
-    ctx32 = olb.create(p, olb.FP32_KAHAN, stream)
-    ctx32.init_fields(*dev_fields)
-    torch.cuda.synchronize()
-    rank_barrier()
-    total32, _ = time_steps(ctx32, args.steps, args.warmup, flush, stream)
-    rank_barrier()
-    total32 = max_over_ranks(total32)
-    m32 = ctx32.moments()
-    prof32 = ctx32.profile(max(3, min(args.steps, 50)))
-    ach32 = STAGE_FLOPS_PER_NODE_FP32 * N / (prof32["stage_ms"] * 1e-3) / 1e12
-    tile32 = ctx32.get_tile()
-    us = max(np.max(np.abs(m64[1])), np.max(np.abs(m64[2])), 1e-300)
-    err32 = {"n": float(np.max(np.abs(m32[0] - m64[0])) / np.max(np.abs(m64[0]))),
-             "u": float(max(np.max(np.abs(m32[1] - m64[1])), np.max(np.abs(m32[2] - m64[2]))) / us),
-             "T": float(np.max(np.abs(m32[3] - m64[3])) / np.max(np.abs(m64[3])))}
-    v32 = job_value(world, N, args.steps, total32)
-    fp32 = {"value": v32, "ms_per_step": total32 / args.steps, "speedup_vs_fp64": v32 / value,
-            "max_rel_err_vs_fp64_after_steps": err32, "steps_compared": args.warmup + args.steps,
-            "roofline": {"kernel": f"k_fused<float,{tile32[0]},{tile32[1]},{tile32[2]}>", "bound": "alu", "achieved": ach32,
-                         "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": ach32 / PEAK_FP32_TFLOPS,
-                         "stage_ms": prof32["stage_ms"]}}
-    ctx32.close()
+    # ---- learned weights (FP64 and FP32 populations)
+    theta = default_theta()
+    learned = {}
+    if theta is not None and not args.no_learned:
+        lsteps = max(1, min(args.steps, args.learned_steps))
+        for name, prec, pk in (("learned_fp64", olb.FP64, peak64), ("learned_fp32", olb.FP32_KAHAN, peak32)):
+            leg, c = timed_leg(olb, p, dev_fields, prec, lsteps, args.warmup, flush, stream, world, pk, weno=1,
+                               theta=theta)
+            leg["steps"] = lsteps
+            leg["speedup_vs_fp64_js"] = leg["value"] / value
+            leg["roofline"]["note"] = ("flops counted as for the Jiang-Shu stage; the network evaluations "
+                                       "are extra work on the FP32 pipe")
+            c.close()
+            del c
+            torch.cuda.empty_cache()
+            learned[name] = leg
 
-    # end to end through the C ABI with pinned host buffers
+    # ---- batch sweep
+    batch = {}
+    if not args.no_batch:
+        batch = run_batch_legs(args, world, stream, peak64, peak32)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    ctx = olb.create(p, olb.FP64, stream)
     host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in fields]
     host_out = [torch.empty((p.ny, p.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
-    e2e_iters = max(3, min(args.steps, 50))
+    e2e_iters = max(3, min(args.steps, 10))
     ctx.init_fields(*[h.numpy() for h in host_in])
     torch.cuda.synchronize()
     rank_barrier()
@@ -334,37 +451,95 @@ def run_ours(args, rank, world):
            "d2h_bytes_per_step": 4 * N * 8,
            "what": "olb_init_fields (host, pinned) + olb_step_async(1) + olb_moments (host, pinned) per step"}
     ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "nodes": N, "grid": [p.nx, p.ny],
-                       "l2": "256 MiB buffer written between timed steps",
+                       "l2": "inputs (10 GB of populations) larger than L2; 256 MiB buffer also written "
+                             "between timed steps",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roof, "fp32_kahan": fp32, "e2e": e2e,
+            "roofline": roof, "fp32": fp32, **learned, **batch, "e2e": e2e,
+            "totals_fp64_gpu": {"mass_initial": tot0[0], "energy_initial": tot0[3],
+                                "mass_after_timed_steps": tot_after[0], "energy_after_timed_steps": tot_after[3],
+                                "mass_rel_change": float((tot_after[0] - tot0[0]) / tot0[0])},
             "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, steps, el, cores = oracle_rate(p, fields, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{steps} whole-grid RK-3 steps of the {p.nx}x{p.ny} workload ({el:.1f} s)"}
+        line.update(oracle_leg(args, p, fields, dev_fields, theta, stream))
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_batch(args, rank, world):
+def oracle_leg(args, p, fields, dev_fields, theta, stream):
+    """Accuracy of every GPU leg against the FP64 oracle on windows, and the
+    oracle's own speed on the host cores (the CPU baseline)."""
+    import torch
+    from paper_1702_01690_gb300 import olb
+    steps = args.check_steps
+    ref, wins, margin, work, secs, cores = oracle_windows(p, fields, steps)
+    out = {"cpu_baseline": {"value": work / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{steps} RK-3 steps of {len(wins)} windows of the {p.nx}x{p.ny} workload "
+                                      f"({work} node-updates, {secs:.1f} s), the windows the accuracy check uses"}}
+    # single-threaded oracle on the first window for a few steps
+    w0 = [wins[0]]
+    x0, y0, wx, wy, wall = w0[0]
+    import oracle
+    from paper_1702_01690_gb300 import inputs
+    oracle.set_threads(1)
+    wp = inputs.RunParams(**{**p.as_dict(), "nx": wx, "ny": wy})
+    if wall is None:
+        wp.side_x = 0
+    o = oracle.Oracle(wp.nx, wp.ny, wp.ds, wp.dt, wp.tau, wp.a, wp.b, wp.sigma, wp.Tw, wp.uw, wp.side_x, wp.side_y)
+    o.init_fields(*crop(fields, x0, y0, wx, wy, p.nx, p.ny, p.side_x == 0))
+    s1 = 2
+    t0 = time.perf_counter()
+    o.step(s1)
+    el = time.perf_counter() - t0
+    o.close()
+    out["cpu_baseline_single_thread"] = {"value": wx * wy * s1 / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                         "sample": f"{s1} RK-3 steps of the {wx}x{wy} window at x0={x0}"}
+    oracle.set_threads(os.cpu_count() or 1)
+    acc = {"steps": steps, "windows": [list(w[:4]) + [w[4] or "bulk"] for w in wins],
+           "interior_margin_nodes": margin}
+    legs = [("fp64", olb.FP64, 0), ("fp32", olb.FP32_KAHAN, 0)]
+    for name, prec, weno in legs:
+        c = olb.create(p, prec, stream)
+        c.init_fields(*dev_fields)
+        assert c.step(steps) == 0
+        acc[name] = window_errors(c.moments(), p, ref, wins, margin)
+        c.close()
+        del c
+        torch.cuda.empty_cache()
+    if theta is not None and not args.no_learned:
+        lsteps = min(steps, 5)
+        lref, lwins, lmargin, _, _, _ = oracle_windows(p, fields, lsteps, theta=theta)
+        acc["learned_steps"] = lsteps
+        for name, prec in (("learned_fp64", olb.FP64), ("learned_fp32", olb.FP32_KAHAN)):
+            c = olb.create(p, prec, stream, weno_mode=olb.WENO_LEARNED)
+            c.set_weno_mlp(theta)
+            c.init_fields(*dev_fields)
+            assert c.step(lsteps) == 0
+            acc[name] = window_errors(c.moments(), p, lref, lwins, lmargin)
+            c.close()
+            del c
+            torch.cuda.empty_cache()
+    out["max_rel_err_vs_fp64_oracle_windows"] = acc
+    return out
+
+
+def run_batch_legs(args, world, stream, peak64, peak32):
     """64 independent runs of uneven sizes (32^2 .. 1024^2 shear and
     longitudinal waves, Laplace drops, planar wall runs; 13.5 M nodes) in one
     persistent launch per stage, replayed from CUDA graphs, shape autotuned.
     The working set (3 x 25 x 13.5 M values) is far larger than L2."""
     import torch
     from paper_1702_01690_gb300 import inputs, olb
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream()
     runs = inputs.batch_sweep()
     nodes = sum(p.nx * p.ny for p, _ in runs)
     out = {}
-    for name, prec in (("fp64", olb.FP64), ("fp32_kahan", olb.FP32_KAHAN)):
+    for name, prec, peak in (("batch_fp64", olb.FP64, peak64), ("batch_fp32", olb.FP32_KAHAN, peak32)):
         b = olb.Batch([p for p, _ in runs], prec, stream)
         for r, (p, fl) in enumerate(runs):
             b.init_fields(r, *fl)
@@ -373,48 +548,40 @@ def run_batch(args, rank, world):
         torch.cuda.synchronize()
         rank_barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
-            e0.record(stream)
-            b.step_async(args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize()
+        e0.record(stream)
+        b.step_async(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
         rank_barrier()
         ms = max_over_ranks(e0.elapsed_time(e1))
         rc, _ = b.status()
         if rc != 0:
             raise RuntimeError(f"batch diverged ({name})")
-        stage_ms = b.profile(2)
-        flops = (STAGE_FLOPS_PER_NODE if prec == olb.FP64 else STAGE_FLOPS_PER_NODE_FP32) * nodes
-        peak = PEAK_FP64_TFLOPS if prec == olb.FP64 else PEAK_FP32_TFLOPS
-        ach = flops / (stage_ms * 1e-3) / 1e12
+        stage_ms = ms / args.steps / 3.0
+        ach = STAGE_FLOPS_PER_NODE * nodes / (stage_ms * 1e-3) / 1e12
         out[name] = {"value": job_value(world, nodes, args.steps, ms), "ms_per_step": ms / args.steps,
-                     "shape": list(shape), "stage_ms": stage_ms,
+                     "runs": len(runs), "nodes": nodes, "shape": list(shape),
                      "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": ach / peak}, "clocks": clk.summary()}
+                                  "frac": ach / peak, "stage_ms": stage_ms}}
         b.close()
         del b
         torch.cuda.empty_cache()
-    line = {"metric": METRIC, "value": out["fp64"]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": out["fp64"]["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batched sweep: 64 runs 32^2..1024^2 (waves, Laplace drops, planar walls)",
-                       "runs": len(runs), "nodes": nodes, "l2": "working set 8.1 GB (FP64) > L2"},
-            "roofline": out["fp64"]["roofline"], "fp32_kahan": out["fp32_kahan"], "fp64": out["fp64"],
-            "gpu_launches": 3 * args.steps}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="planar", choices=["planar", "shear", "laplace", "phase", "batch"])
+    ap.add_argument("--workload", default="phase", choices=["planar", "shear", "laplace", "phase"])
     ap.add_argument("--size", type=int, default=None, help="grid size of the laplace / phase workloads")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--check-steps", type=int, default=20, help="steps of the accuracy check against the oracle")
+    ap.add_argument("--learned-steps", type=int, default=10, help="timed steps of the learned legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -428,10 +595,7 @@ def main():
         import torch.distributed as tdist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         tdist.init_process_group("nccl")
-    if args.workload == "batch":
-        run_batch(args, rank, world)
-    else:
-        run_ours(args, rank, world)
+    run_ours(args, rank, world)
     if world > 1:
         import torch.distributed as tdist
         tdist.destroy_process_group()
