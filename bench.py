@@ -465,7 +465,7 @@ def run_ours(args, rank, world):
             "totals_fp64_gpu": {"mass_initial": tot0[0], "energy_initial": tot0[3],
                                 "mass_after_timed_steps": tot_after[0], "energy_after_timed_steps": tot_after[3],
                                 "mass_rel_change": float((tot_after[0] - tot0[0]) / tot0[0])},
-            "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
+            "gpu_launches": 6 * args.steps, "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line.update(oracle_leg(args, p, fields, dev_fields, theta, stream))
     if rank == 0:

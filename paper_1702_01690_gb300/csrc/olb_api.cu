@@ -181,10 +181,11 @@ struct olb_ctx {
     bool mlp_set;
     double *stage4;             // FP64 [4][ny][nx] staging for host transfers
     double *totals;             // olb_totals: partial sums, then the sums
+    void *fields;               // moments of the stage's input (fields_bytes), read by the stage kernel
     struct Alloc {
         void *ptr;
         size_t bytes;
-    } allocs[8];
+    } allocs[12];
     int nallocs;
     olb_alloc_fn afn;
     olb_free_fn ffn;
@@ -249,7 +250,7 @@ static cudaError_t enqueue_stage(olb_ctx *c, int st, cudaStream_t s)
     const int src_buf[3] = {0, 1, 2};
     return launch_fused(src[st], f0, dst[st], c->status, c->geo, ctx_tab<real>(c), coef, c->tx, c->ty, c->kp,
                         c->p.weno_mode == OLB_WENO_LEARNED ? c->mlp : nullptr,
-                        c->tma_ok ? &c->tma[src_buf[st]] : nullptr, s);
+                        c->tma_ok ? &c->tma[src_buf[st]] : nullptr, c->fields, s);
 }
 
 template <typename real>
@@ -434,8 +435,9 @@ extern "C" int olb_create(const olb_params *p, void *stream, olb_ctx **out)
     c->mlp = p->weno_mode == OLB_WENO_LEARNED ? (float *)ctx_alloc(c, 1348 * sizeof(float)) : nullptr;
     // olb_totals: TOTALS_BLOCKS x 4 partial sums, then the 4 sums
     c->totals = (double *)ctx_alloc(c, (size_t)(4 * TOTALS_BLOCKS + 4) * sizeof(double));
+    c->fields = ctx_alloc(c, fields_bytes(g));
     default_tile(c);
-    bool ok = c->f[0] && c->f[1] && c->f[2] && c->status && c->stage4 && c->totals &&
+    bool ok = c->f[0] && c->f[1] && c->f[2] && c->status && c->stage4 && c->totals && c->fields &&
               (p->weno_mode != OLB_WENO_LEARNED || c->mlp);
     cudaError_t e = cudaSuccess;
     if (ok) {

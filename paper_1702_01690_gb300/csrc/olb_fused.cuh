@@ -146,6 +146,193 @@ __device__ __forceinline__ float face_corr(const float *mlp, float d01, float d1
         return weno5_corr(d01, d12, d23, d34);
 }
 
+// ---------------------------------------------------------------- moments of a node
+// n, u, T and Delta p of one node from its 25 populations (Sec. 2.2; T from
+// the trace of Eq. sigmaq_def; Delta p = n T - p^w, Eq. vdw), and whether they
+// are admissible (finite, n > 0, T > 0, b n < 1).  get(k) returns population
+// k: the value (FP64) or the pair hi + lo (FP32).
+template <typename real>
+struct NodeMoments;
+template <>
+struct NodeMoments<double> {
+    double n, dp, ux, uy, T;
+    bool ok;
+};
+template <>
+struct NodeMoments<float> {
+    float2 n, dp, T, E;  // hi + lo pairs (E = sum |p|^2 f)
+    float ux, uy;
+    bool ok;
+};
+
+template <typename real, typename Get>
+__device__ __forceinline__ NodeMoments<real> node_moments(Get get, const Geo &g, const Tab<real> &t)
+{
+    NodeMoments<real> m;
+    if constexpr (sizeof(real) == 8) {
+        // row and column sums of the 5 x 5 populations; the middle root is 0
+        // (R[2] = R2[2] = 0), so its sums drop out of j and e
+        double sx[NQ], sy[NQ];
+#pragma unroll
+        for (int k1 = 0; k1 < NQ; ++k1) {
+            double s = get(NQ * k1);
+            if (k1 == 0) sy[0] = s;
+            else sy[0] += s;
+#pragma unroll
+            for (int k2 = 1; k2 < NQ; ++k2) {
+                const double v = get(NQ * k1 + k2);
+                s += v;
+                if (k1 == 0) sy[k2] = v;
+                else sy[k2] += v;
+            }
+            sx[k1] = s;
+        }
+        double n = sx[0];
+        double jx = t.R[0] * sx[0];
+        double jy = t.R[0] * sy[0];
+        double en = t.R2[0] * (sx[0] + sy[0]);
+#pragma unroll
+        for (int k = 1; k < NQ; ++k) {
+            n += sx[k];
+            if (k == 2) continue;
+            jx = fma(t.R[k], sx[k], jx);
+            jy = fma(t.R[k], sy[k], jy);
+            en = fma(t.R2[k], sx[k] + sy[k], en);
+        }
+        const double inv_n = recip_nr(n);
+        const double ux = jx * inv_n, uy = jy * inv_n;
+        const double T = 0.5 * fma(en, inv_n, -fma(ux, ux, uy * uy));
+        // Delta p = n T - p^w, p^w = n T / (1 - b n) - a n^2 (Eq. vdw)
+        const double nT = n * T;
+        m.n = n;
+        m.dp = nT - fma(nT, recip_nr(1.0 - g.b * n), -g.a * n * n);
+        m.ux = ux;
+        m.uy = uy;
+        m.T = T;
+        m.ok = (n > 0.0) && (T > 0.0) && (g.b * n < 1.0) && isfinite(n) && isfinite(T) && isfinite(ux) && isfinite(uy);
+    } else {
+        // FP32, compensated storage: row and column sums of the 5 x 5 pairs
+        // as double-float values; n and e = sum |p|^2 f from them in
+        // double-float arithmetic.  j needs FP32 accuracy of j itself:
+        // R_4 (sx_4 - sx_0) + R_3 (sx_3 - sx_1) with the differences of the
+        // double-float sums (R_0 = -R_4, R_1 = -R_3, R_2 = 0).
+        f2 sx[NQ], sy[NQ];
+        {
+            float h[NQ], l[NQ];
+#pragma unroll
+            for (int k1 = 0; k1 < NQ; ++k1) {
+#pragma unroll
+                for (int k2 = 0; k2 < NQ; ++k2) {
+                    const float2 v = get(NQ * k1 + k2);
+                    h[k2] = v.x;
+                    l[k2] = v.y;
+                }
+                sx[k1] = pair_sum5(h, l);
+            }
+#pragma unroll
+            for (int k2 = 0; k2 < NQ; ++k2) {
+#pragma unroll
+                for (int k1 = 0; k1 < NQ; ++k1) {
+                    const float2 v = get(NQ * k1 + k2);
+                    h[k1] = v.x;
+                    l[k1] = v.y;
+                }
+                sy[k2] = pair_sum5(h, l);
+            }
+        }
+        const f2 one{1.0f, 0.0f};
+        const f2 vdw_a = f2_of(g.a), vdw_b = f2_of(g.b);
+        const f2 N = f2_add(f2_add(f2_add(sx[0], sx[4]), f2_add(sx[1], sx[3])), sx[2]);
+        const float jx = fmaf(t.R[4], pdiff(sx[4].hi, sx[4].lo, sx[0].hi, sx[0].lo),
+                              t.R[3] * pdiff(sx[3].hi, sx[3].lo, sx[1].hi, sx[1].lo));
+        const float jy = fmaf(t.R[4], pdiff(sy[4].hi, sy[4].lo, sy[0].hi, sy[0].lo),
+                              t.R[3] * pdiff(sy[3].hi, sy[3].lo, sy[1].hi, sy[1].lo));
+        const f2 S4 = f2_add(f2_add(sx[0], sx[4]), f2_add(sy[0], sy[4]));
+        const f2 S3 = f2_add(f2_add(sx[1], sx[3]), f2_add(sy[1], sy[3]));
+        const f2 R24{t.R2[4], t.R2lo[4]}, R23{t.R2[3], t.R2lo[3]};
+        const f2 Ea = f2_cmul(R24, S4.hi, S4.lo), Eb = f2_cmul(R23, S3.hi, S3.lo);
+        const f2 E = f2_add(fast_two_sum(Ea.hi, Ea.lo), fast_two_sum(Eb.hi, Eb.lo));
+        // u, T and Delta p = n T - p^w = n^2 (a - b T / (1 - b n)) (Eq. vdw):
+        // T and Delta p in double-float arithmetic, so that the stencils of n
+        // and Delta p see ~44-bit values without the FP64 pipe
+        const f2 IN = f2_div(one, N);
+        const float UX = jx * IN.hi, UY = jy * IN.hi;
+        const f2 T = f2_scale(f2_add_f(f2_mul(E, IN), -fmaf(UX, UX, UY * UY)), 0.5f);
+        const f2 BN = f2_mul(vdw_b, N);
+        const f2 Q = f2_div(f2_mul(vdw_b, T), f2_add(one, f2_neg(BN)));
+        const f2 DP = f2_mul(f2_mul(N, N), f2_add(vdw_a, f2_neg(Q)));
+        m.n = make_float2(N.hi, N.lo);
+        m.dp = make_float2(DP.hi, DP.lo);
+        m.T = make_float2(T.hi, T.lo);
+        m.E = make_float2(E.hi, E.lo);
+        m.ux = UX;
+        m.uy = UY;
+        m.ok = (N.hi > 0.0f) && (T.hi > 0.0f) && (BN.hi < 1.0f) && isfinite(N.hi) && isfinite(T.hi) && isfinite(UX) &&
+               isfinite(UY);
+    }
+    return m;
+}
+
+// Fields of the per-node pre-pass (k_fields), [ny][pitch] each: n and
+// Delta p (FP32: hi + lo pairs), u_x, u_y, T (FP32: T a pair, and e = sum
+// |p|^2 f as a pair for the equilibrium's correction).
+template <typename real>
+struct StageFields {
+    using fld = typename FieldT<real>::type;
+    fld *n, *dp, *T, *E;
+    real *ux, *uy;
+};
+
+// Pointers of the fields in a buffer of 5 planes of pitch * ny 8-byte
+// elements (fields_bytes): FP64 n, Delta p, T, u_x, u_y; FP32 n, Delta p,
+// T, e (float2 each), then u_x and u_y (float) sharing the last plane.
+template <typename real>
+__host__ __device__ inline StageFields<real> fields_of(void *base, const Geo &g)
+{
+    StageFields<real> f{};
+    char *b = static_cast<char *>(base);
+    const size_t plane = (size_t)g.plane * 8;
+    f.n = reinterpret_cast<typename FieldT<real>::type *>(b);
+    f.dp = reinterpret_cast<typename FieldT<real>::type *>(b + plane);
+    f.T = reinterpret_cast<typename FieldT<real>::type *>(b + 2 * plane);
+    if constexpr (sizeof(real) == 8) {
+        f.E = nullptr;
+        f.ux = reinterpret_cast<real *>(b + 3 * plane);
+        f.uy = reinterpret_cast<real *>(b + 4 * plane);
+    } else {
+        f.E = reinterpret_cast<typename FieldT<real>::type *>(b + 3 * plane);
+        f.ux = reinterpret_cast<real *>(b + 4 * plane);
+        f.uy = reinterpret_cast<real *>(b + 4 * plane + plane / 2);
+    }
+    return f;
+}
+
+// One thread per node: the moments of f_s, stored for the stage kernel,
+// which then reads them on its tile and halo instead of recomputing them
+// at every halo position; inadmissible moments set bit 0 of the status.
+template <typename real>
+__global__ void __launch_bounds__(256) k_fields(const real *__restrict__ fs, StageFields<real> out, int *status,
+                                                const __grid_constant__ Geo g, const __grid_constant__ Tab<real> t)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)g.nx * g.ny) return;
+    const int j = (int)(idx / g.nx), i = (int)(idx - (long long)j * g.nx);
+    const long long o = (long long)j * g.pitch + i;
+    NodeMoments<real> m;
+    if constexpr (sizeof(real) == 8)
+        m = node_moments<real>([&](int k) { return __ldg(fs + k * g.plane + o); }, g, t);
+    else
+        m = node_moments<real>(
+            [&](int k) { return make_float2(__ldg(fs + k * g.plane + o), __ldg(fs + (NK + k) * g.plane + o)); }, g, t);
+    out.n[o] = m.n;
+    out.dp[o] = m.dp;
+    out.ux[o] = m.ux;
+    out.uy[o] = m.uy;
+    out.T[o] = m.T;
+    if constexpr (sizeof(real) == 4) out.E[o] = m.E;
+    if (!m.ok) atomicOr(status, 1);
+}
+
 // ---------------------------------------------------------------- TMA staging
 // Iterations of the bounded wait for the copy (each try_wait suspends for at
 // most a short, hardware-defined time): far above the microseconds a copy of
@@ -204,15 +391,17 @@ __device__ __forceinline__ bool tma_stage(FusedSmem<real, TX, TY, KP> &sm, const
 // the CTA call it (it synchronises).  ca, cb, cc: the stage's coefficients of
 // f^n, f_s and dt L (Eq. rk3), in the population precision; ca_lo, cb_lo:
 // their remainders (FP32: 1/3 and 2/3 as double-float constants; 0 in FP64).
-// tmap: TMA map of fs for this tile shape (single grids), or nullptr.  g and t may live in parameter space
-// (single grid) or shared memory (batch); mlp: the learned network's
-// parameters in shared memory (LEARNED only).
+// g and t may live in parameter space (single grid) or shared memory
+// (batch); mlp: the learned network's parameters in shared memory (LEARNED
+// only); tmap: TMA map of fs for this tile shape (single grids), or nullptr;
+// fields: the moments of fs from k_fields, or nullptr to compute them here.
 template <typename real, int TX, int TY, int KP, bool LEARNED = false>
 __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, const real *__restrict__ fs,
                                            const real *fn, real *out, int *__restrict__ status, const Geo &g,
                                            const Tab<real> &t, const int x0, const int y0, const real ca,
                                            const real cb, const real cc, const real ca_lo, const real cb_lo,
-                                           const float *mlp = nullptr, const TmaMap *tmap = nullptr)
+                                           const float *mlp = nullptr, const TmaMap *tmap = nullptr,
+                                           const StageFields<real> *fields = nullptr)
 {
     using S = FusedSmem<real, TX, TY, KP>;
     constexpr int NT = S::NT, NN = S::NN, HX = S::HX, HY = S::HY;
@@ -297,7 +486,6 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     // two ghosts extrapolated from them) and stores those two ghosts; both
     // need the phase-1 populations only, and the FP64 units of the
     // sub-partitions with fewer moment warps have room.
-    const f2 vdw_a = f2_of(g.a), vdw_b = f2_of(g.b);  // FP32 variant only
     const bool x_lo = g.walls && x0 == 0;                // ghost columns at x = 0
     const bool x_hi = g.walls && (x0 + TX + 3 >= g.nx);  // ghost columns at x = nx ds
     const bool left_wall = x_lo && g.wall_lo;
@@ -305,121 +493,48 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     // wall-flux items start on the first warp after the moment positions
     constexpr int e_flux = (HY * (HX - 2) + 31) / 32 * 32;
     const int nflux = ((int)left_wall + (int)right_wall) * TY * 16;
-    for (int e = tid; e < HY * (HX - 2); e += NT) {
-        const int r = e / (HX - 2), c = e - r * (HX - 2) + 1;
-        const int gx = x0 - 4 + c, gyr = y0 - 3 + r;
-        if (g.walls && (gx < 0 || gx >= g.nx)) continue;
-        if (g.spec_y && (gyr < 0 || gyr >= g.ny)) continue;
-        const int tr = r - 3, tc = c - 4;
-        const bool tile_node = tr >= 0 && tr < TY && tc >= 0 && tc < TX;
-        const bool own = tile_node && x0 + tc < g.nx && y0 + tr < g.ny;
-        if constexpr (sizeof(real) == 8) {
-            // row and column sums of the 5 x 5 populations; the middle root
-            // is 0 (R[2] = R2[2] = 0), so its sums drop out of j and e
-            double sx[NQ], sy[NQ];
-#pragma unroll
-            for (int k1 = 0; k1 < NQ; ++k1) {
-                double s = (double)sm.pop[NQ * k1][r][c];
-                if (k1 == 0) sy[0] = s;
-                else sy[0] += s;
-#pragma unroll
-                for (int k2 = 1; k2 < NQ; ++k2) {
-                    const double v = (double)sm.pop[NQ * k1 + k2][r][c];
-                    s += v;
-                    if (k1 == 0) sy[k2] = v;
-                    else sy[k2] += v;
-                }
-                sx[k1] = s;
+    if (fields != nullptr) {
+        // moments from the per-node pre-pass (k_fields): n and Delta p on the
+        // region, u, T (FP32: and e) at the tile nodes
+        for (int e = tid; e < HY * (HX - 2); e += NT) {
+            const int r = e / (HX - 2), c = e - r * (HX - 2) + 1;
+            const int gx = x0 - 4 + c, gyr = y0 - 3 + r;
+            if (g.walls && (gx < 0 || gx >= g.nx)) continue;
+            if (g.spec_y && (gyr < 0 || gyr >= g.ny)) continue;
+            const long long o = (long long)wrap(gyr, g.ny) * g.pitch + wrap(gx, g.nx);
+            sm.n[r][c] = fields->n[o];
+            sm.dp[r][c] = fields->dp[o];
+            const int tr = r - 3, tc = c - 4;
+            if (tr >= 0 && tr < TY && tc >= 0 && tc < TX) {
+                sm.ux[tr][tc] = fields->ux[o];
+                sm.uy[tr][tc] = fields->uy[o];
+                sm.T[tr][tc] = fields->T[o];
+                if constexpr (sizeof(real) == 4) sm.eng[tr][tc] = fields->E[o];
             }
-            double n = sx[0];
-            double jx = (double)t.R[0] * sx[0];
-            double jy = (double)t.R[0] * sy[0];
-            double en = (double)t.R2[0] * (sx[0] + sy[0]);
-#pragma unroll
-            for (int k = 1; k < NQ; ++k) {
-                n += sx[k];
-                if (k == 2) continue;
-                jx = fma((double)t.R[k], sx[k], jx);
-                jy = fma((double)t.R[k], sy[k], jy);
-                en = fma((double)t.R2[k], sx[k] + sy[k], en);
-            }
-            const double inv_n = recip_nr(n);
-            const double ux = jx * inv_n, uy = jy * inv_n;
-            const double T = 0.5 * fma(en, inv_n, -fma(ux, ux, uy * uy));
-            // Delta p = n T - p^w, p^w = n T / (1 - b n) - a n^2 (Eq. vdw)
-            const double nT = n * T;
-            sm.n[r][c] = make_field(n, real(0));
-            sm.dp[r][c] = make_field(nT - fma(nT, recip_nr(1.0 - g.b * n), -g.a * n * n), real(0));
+        }
+    } else {
+        for (int e = tid; e < HY * (HX - 2); e += NT) {
+            const int r = e / (HX - 2), c = e - r * (HX - 2) + 1;
+            const int gx = x0 - 4 + c, gyr = y0 - 3 + r;
+            if (g.walls && (gx < 0 || gx >= g.nx)) continue;
+            if (g.spec_y && (gyr < 0 || gyr >= g.ny)) continue;
+            const int tr = r - 3, tc = c - 4;
+            const bool tile_node = tr >= 0 && tr < TY && tc >= 0 && tc < TX;
+            const bool own = tile_node && x0 + tc < g.nx && y0 + tr < g.ny;
+            NodeMoments<real> m;
+            if constexpr (sizeof(real) == 8)
+                m = node_moments<real>([&](int k) { return sm.pop[k][r][c]; }, g, t);
+            else
+                m = node_moments<real>([&](int k) { return make_float2(sm.pop[k][r][c], sm.pl.lo[k][r][c]); }, g,
+                                       t);
+            sm.n[r][c] = m.n;
+            sm.dp[r][c] = m.dp;
             if (tile_node) {
-                sm.ux[tr][tc] = (real)ux;
-                sm.uy[tr][tc] = (real)uy;
-                sm.T[tr][tc] = T;
-                if (own) {
-                    const bool ok = (n > 0.0) && (T > 0.0) && (g.b * n < 1.0) && isfinite(n) && isfinite(T) &&
-                                    isfinite(ux) && isfinite(uy);
-                    if (!ok) atomicOr(status, 1);
-                }
-            }
-        } else {
-            // FP32, compensated storage: row and column sums of the 5 x 5 pairs
-            // as double-float values; n and e = sum |p|^2 f from them in
-            // double-float arithmetic.  j needs FP32 accuracy of j itself:
-            // R_4 (sx_4 - sx_0) + R_3 (sx_3 - sx_1) with the differences of
-            // the double-float sums (R_0 = -R_4, R_1 = -R_3, R_2 = 0).
-            f2 sx[NQ], sy[NQ];
-            {
-                float h[NQ], l[NQ];
-#pragma unroll
-                for (int k1 = 0; k1 < NQ; ++k1) {
-#pragma unroll
-                    for (int k2 = 0; k2 < NQ; ++k2) {
-                        h[k2] = sm.pop[NQ * k1 + k2][r][c];
-                        l[k2] = sm.pl.lo[NQ * k1 + k2][r][c];
-                    }
-                    sx[k1] = pair_sum5(h, l);
-                }
-#pragma unroll
-                for (int k2 = 0; k2 < NQ; ++k2) {
-#pragma unroll
-                    for (int k1 = 0; k1 < NQ; ++k1) {
-                        h[k1] = sm.pop[NQ * k1 + k2][r][c];
-                        l[k1] = sm.pl.lo[NQ * k1 + k2][r][c];
-                    }
-                    sy[k2] = pair_sum5(h, l);
-                }
-            }
-            const f2 one{1.0f, 0.0f};
-            const f2 N = f2_add(f2_add(f2_add(sx[0], sx[4]), f2_add(sx[1], sx[3])), sx[2]);
-            const float jx = fmaf((float)t.R[4], pdiff(sx[4].hi, sx[4].lo, sx[0].hi, sx[0].lo),
-                                  (float)t.R[3] * pdiff(sx[3].hi, sx[3].lo, sx[1].hi, sx[1].lo));
-            const float jy = fmaf((float)t.R[4], pdiff(sy[4].hi, sy[4].lo, sy[0].hi, sy[0].lo),
-                                  (float)t.R[3] * pdiff(sy[3].hi, sy[3].lo, sy[1].hi, sy[1].lo));
-            const f2 S4 = f2_add(f2_add(sx[0], sx[4]), f2_add(sy[0], sy[4]));
-            const f2 S3 = f2_add(f2_add(sx[1], sx[3]), f2_add(sy[1], sy[3]));
-            const f2 R24{(float)t.R2[4], (float)t.R2lo[4]}, R23{(float)t.R2[3], (float)t.R2lo[3]};
-            const f2 Ea = f2_cmul(R24, S4.hi, S4.lo), Eb = f2_cmul(R23, S3.hi, S3.lo);
-            const f2 E = f2_add(fast_two_sum(Ea.hi, Ea.lo), fast_two_sum(Eb.hi, Eb.lo));
-            // u, T and Delta p = n T - p^w = n^2 (a - b T / (1 - b n)) (Eq. vdw):
-            // T and Delta p in double-float arithmetic, so that the stencils of
-            // n and Delta p see ~44-bit values without the FP64 pipe
-            const f2 IN = f2_div(one, N);
-            const float UX = jx * IN.hi, UY = jy * IN.hi;
-            const f2 T = f2_scale(f2_add_f(f2_mul(E, IN), -fmaf(UX, UX, UY * UY)), 0.5f);
-            const f2 BN = f2_mul(vdw_b, N);
-            const f2 Q = f2_div(f2_mul(vdw_b, T), f2_add(one, f2_neg(BN)));
-            const f2 DP = f2_mul(f2_mul(N, N), f2_add(vdw_a, f2_neg(Q)));
-            sm.n[r][c] = make_float2(N.hi, N.lo);
-            sm.dp[r][c] = make_float2(DP.hi, DP.lo);
-            if (tile_node) {
-                sm.ux[tr][tc] = UX;
-                sm.uy[tr][tc] = UY;
-                sm.T[tr][tc] = make_float2(T.hi, T.lo);
-                sm.eng[tr][tc] = make_float2(E.hi, E.lo);
-                if (own) {
-                    const bool ok = (N.hi > 0.0f) && (T.hi > 0.0f) && (BN.hi < 1.0f) && isfinite(N.hi) &&
-                                    isfinite(T.hi) && isfinite(UX) && isfinite(UY);
-                    if (!ok) atomicOr(status, 1);
-                }
+                sm.ux[tr][tc] = m.ux;
+                sm.uy[tr][tc] = m.uy;
+                sm.T[tr][tc] = m.T;
+                if constexpr (sizeof(real) == 4) sm.eng[tr][tc] = m.E;
+                if (own && !m.ok) atomicOr(status, 1);
             }
         }
     }
@@ -977,7 +1092,8 @@ __global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT,
                                                  FusedSmem<real, TX, TY, KP>::NT, LEARNED))
 k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
         const __grid_constant__ Geo g, const __grid_constant__ Tab<real> t, real ca, real cb, real cc, real ca_lo,
-        real cb_lo, const float *__restrict__ mlp, const __grid_constant__ TmaArg tma)
+        real cb_lo, const float *__restrict__ mlp, const __grid_constant__ TmaArg tma,
+        const __grid_constant__ StageFields<real> fields)
 {
     // 128-byte aligned: the TMA copy of phase 1 lands at offset 0
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -989,7 +1105,8 @@ k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict_
         // made visible by the first barrier inside stage_tile
     }
     stage_tile<real, TX, TY, KP, LEARNED>(sm, fs, fn, out, status, g, t, blockIdx.x * TX, blockIdx.y * TY, ca, cb, cc,
-                                          ca_lo, cb_lo, mlp_sm, tma.on ? &tma.map : nullptr);
+                                          ca_lo, cb_lo, mlp_sm, tma.on ? &tma.map : nullptr,
+                                          fields.n ? &fields : nullptr);
 }
 
 // Batch of independent runs (uneven grid sizes, own parameters): a
@@ -1061,7 +1178,8 @@ cudaError_t fused_prepare_one()
 
 template <typename real, int TX, int TY, int KP, bool LEARNED = false>
 cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *status, const Geo &g,
-                             const Tab<real> &t, StageCoef c, const float *mlp, const TmaMap *tmap, cudaStream_t s)
+                             const Tab<real> &t, StageCoef c, const float *mlp, const TmaMap *tmap, void *fields,
+                             cudaStream_t s)
 {
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
     TmaArg tma{};
@@ -1069,9 +1187,16 @@ cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *sta
         tma.map = *tmap;
         tma.on = 1;
     }
+    StageFields<real> fl{};
+    if (fields) {
+        // the moments of fs first (one thread per node), then the stage
+        fl = fields_of<real>(fields, g);
+        const long long N = (long long)g.nx * g.ny;
+        k_fields<real><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(fs, fl, status, g, t);
+    }
     k_fused<real, TX, TY, KP, LEARNED><<<grid, FusedSmem<real, TX, TY, KP>::NT, fused_smem_bytes<real, TX, TY, KP, LEARNED>(), s>>>(
         fs, fn, out, status, g, t, (real)c.ca, (real)c.cb, (real)c.cc, (real)(c.ca - (double)(real)c.ca),
-        (real)(c.cb - (double)(real)c.cb), mlp, tma);
+        (real)(c.cb - (double)(real)c.cb), mlp, tma, fl);
     return cudaGetLastError();
 }
 
@@ -1112,10 +1237,10 @@ cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, in
     if (learned && tx == A && ty == B && kp == C) return fused_prepare_one<real, A, B, C, true>();
 #define OLB_FUSED_LAUNCH_CASE(real, A, B, C)           \
     if (!mlp && tx == A && ty == B && kp == C)          \
-        return fused_launch_one<real, A, B, C>(fs, fn, out, status, g, t, c, mlp, tma, s);
+        return fused_launch_one<real, A, B, C>(fs, fn, out, status, g, t, c, mlp, tma, fields, s);
 #define OLB_FUSED_LAUNCH_LEARNED(real, A, B, C)                 \
     if (mlp && tx == A && ty == B && kp == C)                   \
-        return fused_launch_one<real, A, B, C, true>(fs, fn, out, status, g, t, c, mlp, tma, s);
+        return fused_launch_one<real, A, B, C, true>(fs, fn, out, status, g, t, c, mlp, tma, fields, s);
 #define OLB_FUSED_BATCH_CASE(real, A, B, C)                                                                  \
     if (tx == A && ty == B && kp == C)                                                                       \
         return fused_batch_launch_one<real, A, B, C>(fs, fn, out, status, runs, tile_start, nruns, total, c, s);
@@ -1128,7 +1253,7 @@ cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, in
     }                                                                                                         \
     cudaError_t launch_fused(const real *fs, const real *fn, real *out, int *status, const Geo &g,            \
                              const Tab<real> &t, StageCoef c, int tx, int ty, int kp, const float *mlp,       \
-                             const TmaMap *tma, cudaStream_t s)                                               \
+                             const TmaMap *tma, void *fields, cudaStream_t s)                                 \
     {                                                                                                         \
         OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_LAUNCH_CASE)                                                    \
         OLB_FUSED_LEARNED_CASES(real, OLB_FUSED_LAUNCH_LEARNED)                                               \

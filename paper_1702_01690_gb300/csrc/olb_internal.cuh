@@ -94,12 +94,14 @@ struct StageCoef {
 };
 
 // Launchers, one set per precision (olb_fp64.cu, olb_fp32.cu).  Output
-// pointers of launch_moments_out may be NULL to skip a field.
+// pointers of launch_moments_out may be NULL to skip a field.  launch_fused
+// with fields != NULL (a buffer of fields_bytes(g)) runs the per-node
+// moments pre-pass first and lets the stage kernel read its results.
 #define OLB_DECLARE_LAUNCHERS(real)                                                                    \
     cudaError_t prepare_fused(real *, int tx, int ty, int kp, bool learned);                           \
     cudaError_t launch_fused(const real *fs, const real *fn, real *out, int *status, const Geo &g,     \
                              const Tab<real> &t, StageCoef c, int tx, int ty, int kp,                  \
-                             const float *mlp, const TmaMap *tma, cudaStream_t s);                     \
+                             const float *mlp, const TmaMap *tma, void *fields, cudaStream_t s);       \
     cudaError_t launch_fused_batch(const real *fs, const real *fn, real *out, int *status,             \
                                    const void *runs, const int *tile_start, int nruns, int total,      \
                                    StageCoef c, int tx, int ty, int kp, cudaStream_t s);               \
@@ -116,6 +118,10 @@ struct StageCoef {
 
 OLB_DECLARE_LAUNCHERS(double)
 OLB_DECLARE_LAUNCHERS(float)
+
+// Bytes of the per-node moment fields of the stage pre-pass: 5 planes of
+// pitch * ny 8-byte elements.
+inline size_t fields_bytes(const Geo &g) { return (size_t)5 * g.plane * 8; }
 
 // Global sums (olb_totals): fixed grid of the first reduction pass, whose
 // per-block partial sums (4 each) the second pass adds in a fixed order.

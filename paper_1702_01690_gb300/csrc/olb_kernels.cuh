@@ -54,6 +54,19 @@ __device__ __forceinline__ double recip_nr(double d)
     return fma(r, e, r);
 }
 
+// The same with one Newton-Raphson step: measured on a GB300 over 2^20
+// random d, the seed is within 2^-19.9 of 1/d and one step within 2^-39.9
+// (9.8e-13).  Used for the normalisation of the WENO weights only, where a
+// relative error of 1e-12 in the weights moves a face value by 1e-12 of its
+// correction (the face value minus its upwind node), far below rounding of
+// the state; moments and pressures keep recip_nr.
+__device__ __forceinline__ double recip_nr1(double d)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    return fma(r, fma(-d, r, 1.0), r);
+}
+
 // v0..v4 = f_{i-2} .. f_{i+2} in the upwind orientation; returns the WENO-5
 // interface value sum_q wbar_q Fhat^q (without p/m).
 //
@@ -71,7 +84,8 @@ __device__ __forceinline__ double recip_nr(double d)
 //
 // Weights: wbar_q is proportional to delta_q / sigma_q^2.  Multiplying every
 // term by 10 (sigma_1 sigma_2 sigma_3)^2 gives weights proportional to
-// A_q = 10 delta_q (prod_{r != q} sigma_r)^2, which needs one reciprocal,
+// A_q = 10 delta_q (prod_{r != q} sigma_r)^2, which needs one reciprocal
+// (recip_nr1),
 // equals the table row for a single vanishing indicator, and is 0/0 only when
 // two or three vanish; those cases take Table tab:weno (the ideal weights of
 // the vanishing set).  If the products underflow without an exact zero the
@@ -112,7 +126,7 @@ __device__ __forceinline__ double weno5_core(double d01, double d12, double d23,
         }
         den = A1 + A2 + A3;
     }
-    return fma(fma(A1, G1, fma(A2, G2, A3 * G3)), recip_nr(6.0 * den), v2);
+    return fma(fma(A1, G1, fma(A2, G2, A3 * G3)), recip_nr1(6.0 * den), v2);
 }
 __device__ __forceinline__ double weno5(double v0, double v1, double v2, double v3, double v4)
 {

@@ -136,7 +136,7 @@ extern "C" int olb_step_static(const olb_params *p, void *stream, double *f, int
     double *dst[3] = {f1, f2, f};
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k)
         for (int st = 0; st < 3 && e == cudaSuccess; ++st)
-            e = launch_fused(src[st], f, dst[st], status, g, tab, coef[st], tx, ty, kp, nullptr, nullptr, s);
+            e = launch_fused(src[st], f, dst[st], status, g, tab, coef[st], tx, ty, kp, nullptr, nullptr, nullptr, s);
     int hstatus = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
