@@ -20,6 +20,19 @@ constexpr int MLP_P = 1347;
 // the ideal weights and keep 5th order) the Jiang-Shu weights are used.
 constexpr double MLP_GUARD = 0.9;
 
+// tanh(x) = sign(x) (1 - 2 / (exp(2 |x|) + 1)), with exp(2 |x|) = 2^(2 |x| / ln 2)
+// and the reciprocal from the special-function unit (ex2.approx.ftz.f32,
+// rcp.approx.ftz.f32): 6 instructions instead of an accurate tanhf, with an
+// absolute error of ~1e-7 (the network's forward pass is checked against the
+// FP64 network at 2e-6 in the tests); exp overflowing to +inf gives 1.
+__device__ __forceinline__ float tanh_fast(float x)
+{
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fabsf(x) * 2.8853900817779268f));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.0f));
+    return copysignf(fmaf(-2.0f, r, 1.0f), x);
+}
+
 // Weights of one stencil; th points to the parameters (shared memory in the
 // stage kernel).  x: normalised stencil.
 __device__ __forceinline__ void mlp_weights(const float *__restrict__ th, const float x[MLP_IN], float w[MLP_OUT])
@@ -30,7 +43,7 @@ __device__ __forceinline__ void mlp_weights(const float *__restrict__ th, const 
         float a = th[MLP_B1 + j];
 #pragma unroll
         for (int q = 0; q < MLP_IN; ++q) a = fmaf(th[MLP_W1 + j * MLP_IN + q], x[q], a);
-        h1[j] = tanhf(a);
+        h1[j] = tanh_fast(a);
     }
     float z0 = th[MLP_B3 + 0], z1 = th[MLP_B3 + 1], z2 = th[MLP_B3 + 2];
 #pragma unroll 4
@@ -45,7 +58,7 @@ __device__ __forceinline__ void mlp_weights(const float *__restrict__ th, const 
             a = fmaf(r.z, h1[4 * k4 + 2], a);
             a = fmaf(r.w, h1[4 * k4 + 3], a);
         }
-        const float h2 = tanhf(a);
+        const float h2 = tanh_fast(a);
         z0 = fmaf(th[MLP_W3 + 0 * MLP_H + j], h2, z0);
         z1 = fmaf(th[MLP_W3 + 1 * MLP_H + j], h2, z1);
         z2 = fmaf(th[MLP_W3 + 2 * MLP_H + j], h2, z2);
