@@ -71,7 +71,11 @@ VALUES_PER_NODE_STEP = 200
 # grid is too large to capture), scaled by 4 to the 16.8 M nodes of the
 # 4096^2 grid (traffic grows with the node count).  Any other kernel or
 # workload reports null.
-DRAM_TRAFFIC_PER_LAUNCH = {}
+DRAM_TRAFFIC_PER_LAUNCH = {
+    # 2048^2, stages 1, 2, 3: 1.819, 2.665, 2.654 GB (FP64) and 1.817, 2.664, 2.651 GB (FP32); mean x 4
+    ("phase", None, "k_fused<double,8,8,4>"): 4 * (1.819 + 2.665 + 2.654) / 3 * 1e9,
+    ("phase", None, "k_fused<float,8,8,8>"): 4 * (1.817 + 2.664 + 2.651) / 3 * 1e9,
+}
 
 
 def load_peaks():
@@ -142,6 +146,10 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # let the sampler start (its first query) before the timed region
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.05)
         except Exception:
             self.proc = None
         return self
@@ -403,6 +411,7 @@ def run_ours(args, rank, world):
     fp32, c32 = timed_leg(olb, p, dev_fields, olb.FP32_KAHAN, args.steps, args.warmup, flush, stream, world, peak32)
     fp32["speedup_vs_fp64"] = fp32["value"] / value
     fp32["roofline"]["peak_source"] = f"FP32 lanes x max SM clock: 128/SM x {sms} SMs x {mhz:.0f} MHz x 2 flop"
+    fp32["roofline"]["traffic"] = DRAM_TRAFFIC_PER_LAUNCH.get((args.workload, args.size, fp32["roofline"]["kernel"]))
     c32.close()
     del c32
     torch.cuda.empty_cache()

@@ -46,6 +46,10 @@ struct olb_batch {
     void *runs = nullptr;                // BatchRun<real>[count]
     int *tile_start = nullptr;           // [count + 1]
     double *stage4 = nullptr;            // FP64 [4][max nodes] staging
+    void *fields = nullptr;              // stage fields of every run (moments pre-pass)
+    std::vector<long long> foff;         // byte offset of each run's fields
+    long long *node_start = nullptr;     // [count + 1] prefix sum of the runs' node counts
+    long long total_nodes = 0;
     long long max_nodes = 0;
     int tx = 16, ty = 8, kp = 2, total_tiles = 0;
     std::vector<char> init;
@@ -87,9 +91,9 @@ static cudaError_t batch_upload(olb_batch *b)
         start[r] = acc;
         acc += ntx * nty;
         if (b_fp64(b))
-            batch_run_fill((double *)nullptr, host.data() + rb * r, g, b->tab64[r], b->off[r], ntx);
+            batch_run_fill((double *)nullptr, host.data() + rb * r, g, b->tab64[r], b->off[r], b->foff[r], ntx);
         else
-            batch_run_fill((float *)nullptr, host.data() + rb * r, g, b->tab32[r], b->off[r], ntx);
+            batch_run_fill((float *)nullptr, host.data() + rb * r, g, b->tab32[r], b->off[r], b->foff[r], ntx);
     }
     start[b->count] = acc;
     b->total_tiles = acc;
@@ -115,7 +119,7 @@ static cudaError_t batch_stage(olb_batch *b, int st, cudaStream_t s)
     // the dt-proportional coefficient is multiplied by each run's own dt
     const StageCoef coef[3] = {{0.0, 1.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}};
     return launch_fused_batch(src[st], f0, dst[st], b->status, b->runs, b->tile_start, b->count, b->total_tiles,
-                              coef[st], b->tx, b->ty, b->kp, s);
+                              coef[st], b->tx, b->ty, b->kp, b->fields, b->node_start, b->total_nodes, s);
 }
 
 static cudaError_t batch_enqueue_steps(olb_batch *b, int n, cudaStream_t s)
@@ -152,6 +156,8 @@ static void batch_free(olb_batch *b)
     cudaFree(b->runs);
     cudaFree(b->tile_start);
     cudaFree(b->stage4);
+    cudaFree(b->fields);
+    cudaFree(b->node_start);
 }
 
 static bool batch_shape_index(int tx, int ty, int kp, int *k)
@@ -194,7 +200,9 @@ extern "C" int olb_batch_create(const olb_params *runs, int count, void *stream,
     b->tab64.resize(count);
     b->tab32.resize(count);
     b->init.assign(count, 0);
-    long long acc = 0;
+    b->foff.resize(count);
+    long long acc = 0, facc = 0;
+    std::vector<long long> nstart(count + 1, 0);
     for (int r = 0; r < count; ++r) {
         const olb_params *p = &runs[r];
         Geo &g = b->geo[r];
@@ -215,6 +223,9 @@ extern "C" int olb_batch_create(const olb_params *runs, int count, void *stream,
         fill_tab<float>(&b->tab32[r], h, p->Tw, p->uw);
         b->off[r] = acc;
         acc += ((long long)(b_fp64(b) ? pop_planes<double>() : pop_planes<float>()) * g.plane + 63) / 64 * 64;
+        b->foff[r] = facc;
+        facc += ((long long)fields_bytes(g) + 255) / 256 * 256;
+        nstart[r + 1] = nstart[r] + (long long)g.nx * g.ny;
         b->max_nodes = std::max(b->max_nodes, (long long)g.nx * g.ny);
     }
     b->total_elems = acc;
@@ -234,6 +245,12 @@ extern "C" int olb_batch_create(const olb_params *runs, int count, void *stream,
     if (e == cudaSuccess) e = cudaMalloc(&b->runs, rb * count);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->tile_start, (size_t)(count + 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->stage4, (size_t)4 * b->max_nodes * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->fields, (size_t)facc);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->node_start, (size_t)(count + 1) * sizeof(long long));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->node_start, nstart.data(), (size_t)(count + 1) * sizeof(long long),
+                            cudaMemcpyHostToDevice, b->stream);
+    b->total_nodes = nstart[count];
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMemsetAsync(b->f[k], 0, (size_t)acc * b->elt, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, (size_t)count * sizeof(int), b->stream);
     if (e == cudaSuccess) e = batch_prepare(b);

@@ -1121,7 +1121,8 @@ template <typename real>
 struct __align__(16) BatchRun {
     Geo g;
     Tab<real> t;
-    long long off;
+    long long off;   // populations: element offset in the three buffers
+    long long foff;  // stage fields: byte offset in the fields buffer
     int ntx, pad;
 };
 static_assert(sizeof(BatchRun<double>) % 16 == 0, "BatchRun<double> must be a whole number of int4 words");
@@ -1138,7 +1139,7 @@ __global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT,
                                                         FusedSmem<real, TX, TY, KP>::NT) > 1 ? 2 : 1))
 k_fused_batch(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
               const BatchRun<real> *__restrict__ runs, const int *__restrict__ tile_start, int nruns, int total,
-              real ca, real cb, real ccoef, real ca_lo, real cb_lo)
+              real ca, real cb, real ccoef, real ca_lo, real cb_lo, char *fields)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<FusedSmem<real, TX, TY, KP> *>(smem_raw);
@@ -1159,9 +1160,52 @@ k_fused_batch(const real *__restrict__ fs, const real *fn, real *out, int *__res
         __syncthreads();
         const int lt = item - __ldg(tile_start + lo);
         const int x0 = (lt % run.ntx) * TX, y0 = (lt / run.ntx) * TY;
+        const StageFields<real> fl = fields ? fields_of<real>(fields + run.foff, run.g) : StageFields<real>{};
         stage_tile<real, TX, TY, KP>(sm, fs + run.off, fn + run.off, out + run.off, status + lo, run.g, run.t, x0, y0,
-                                     ca, cb, ccoef * (real)run.g.dt, ca_lo, cb_lo);
+                                     ca, cb, ccoef * (real)run.g.dt, ca_lo, cb_lo, nullptr, nullptr,
+                                     fields ? &fl : nullptr);
         __syncthreads();  // the next item overwrites the shared staging
+    }
+}
+
+// The moments pre-pass for a batch: one thread per node of every run (a
+// grid-stride loop over the prefix sum node_start of the runs' node counts),
+// writing each run's fields at its offset of the fields buffer.
+template <typename real>
+__global__ void __launch_bounds__(256) k_fields_batch(const real *__restrict__ fs, char *fields,
+                                                      const BatchRun<real> *__restrict__ runs,
+                                                      const long long *__restrict__ node_start, int nruns,
+                                                      long long total, int *status)
+{
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nruns - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(node_start + mid) <= idx) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchRun<real> &run = runs[lo];
+        const Geo &g = run.g;
+        const long long q = idx - __ldg(node_start + lo);
+        const int j = (int)(q / g.nx), i = (int)(q - (long long)j * g.nx);
+        const long long o = (long long)j * g.pitch + i;
+        const real *f = fs + run.off;
+        NodeMoments<real> m;
+        if constexpr (sizeof(real) == 8)
+            m = node_moments<real>([&](int k) { return __ldg(f + k * g.plane + o); }, g, run.t);
+        else
+            m = node_moments<real>(
+                [&](int k) { return make_float2(__ldg(f + k * g.plane + o), __ldg(f + (NK + k) * g.plane + o)); }, g,
+                run.t);
+        const StageFields<real> out = fields_of<real>(fields + run.foff, g);
+        out.n[o] = m.n;
+        out.dp[o] = m.dp;
+        out.ux[o] = m.ux;
+        out.uy[o] = m.uy;
+        out.T[o] = m.T;
+        if constexpr (sizeof(real) == 4) out.E[o] = m.E;
+        if (!m.ok) atomicOr(status + lo, 1);
     }
 }
 
@@ -1202,7 +1246,8 @@ cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *sta
 
 template <typename real, int TX, int TY, int KP>
 cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, int *status, const void *runs,
-                                   const int *tile_start, int nruns, int total, StageCoef c, cudaStream_t s)
+                                   const int *tile_start, int nruns, int total, StageCoef c, void *fields,
+                                   const long long *node_start, long long total_nodes, cudaStream_t s)
 {
     static int ctas_per_sm[64] = {};
     int dev = 0;
@@ -1217,9 +1262,16 @@ cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, in
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = total < per * sms ? total : per * sms;
     if (grid < 1) return cudaSuccess;
+    if (fields && total_nodes > 0) {
+        const long long want = (total_nodes + 255) / 256, cap = 8LL * sms * 8;
+        k_fields_batch<real><<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(
+            fs, static_cast<char *>(fields), static_cast<const BatchRun<real> *>(runs), node_start, nruns, total_nodes,
+            status);
+    }
     k_fused_batch<real, TX, TY, KP><<<grid, FusedSmem<real, TX, TY, KP>::NT, sizeof(FusedSmem<real, TX, TY, KP>), s>>>(
         fs, fn, out, status, static_cast<const BatchRun<real> *>(runs), tile_start, nruns, total, (real)c.ca,
-        (real)c.cb, (real)c.cc, (real)(c.ca - (double)(real)c.ca), (real)(c.cb - (double)(real)c.cb));
+        (real)c.cb, (real)c.cc, (real)(c.ca - (double)(real)c.ca), (real)(c.cb - (double)(real)c.cb),
+        static_cast<char *>(fields));
     return cudaGetLastError();
 }
 
@@ -1243,7 +1295,8 @@ cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, in
         return fused_launch_one<real, A, B, C, true>(fs, fn, out, status, g, t, c, mlp, tma, fields, s);
 #define OLB_FUSED_BATCH_CASE(real, A, B, C)                                                                  \
     if (tx == A && ty == B && kp == C)                                                                       \
-        return fused_batch_launch_one<real, A, B, C>(fs, fn, out, status, runs, tile_start, nruns, total, c, s);
+        return fused_batch_launch_one<real, A, B, C>(fs, fn, out, status, runs, tile_start, nruns, total, c,     \
+                                                     fields, node_start, total_nodes, s);
 #define OLB_DEFINE_FUSED(real)                                                                                \
     cudaError_t prepare_fused(real *, int tx, int ty, int kp, bool learned)                                   \
     {                                                                                                         \
@@ -1261,18 +1314,21 @@ cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, in
     }                                                                                                         \
     cudaError_t launch_fused_batch(const real *fs, const real *fn, real *out, int *status, const void *runs,  \
                                    const int *tile_start, int nruns, int total, StageCoef c, int tx, int ty,  \
-                                   int kp, cudaStream_t s)                                                    \
+                                   int kp, void *fields, const long long *node_start, long long total_nodes,  \
+                                   cudaStream_t s)                                                            \
     {                                                                                                         \
         OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_BATCH_CASE)                                                     \
         return cudaErrorInvalidValue;                                                                         \
     }                                                                                                         \
     size_t batch_run_bytes(real *) { return sizeof(BatchRun<real>); }                                         \
-    void batch_run_fill(real *, void *dst, const Geo &g, const Tab<real> &t, long long off, int ntx)         \
+    void batch_run_fill(real *, void *dst, const Geo &g, const Tab<real> &t, long long off, long long foff,   \
+                        int ntx)                                                                              \
     {                                                                                                         \
         BatchRun<real> r{};                                                                                   \
         r.g = g;                                                                                              \
         r.t = t;                                                                                              \
         r.off = off;                                                                                          \
+        r.foff = foff;                                                                                        \
         r.ntx = ntx;                                                                                          \
         *static_cast<BatchRun<real> *>(dst) = r;                                                              \
     }

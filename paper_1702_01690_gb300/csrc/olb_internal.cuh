@@ -104,9 +104,11 @@ struct StageCoef {
                              const float *mlp, const TmaMap *tma, void *fields, cudaStream_t s);       \
     cudaError_t launch_fused_batch(const real *fs, const real *fn, real *out, int *status,             \
                                    const void *runs, const int *tile_start, int nruns, int total,      \
-                                   StageCoef c, int tx, int ty, int kp, cudaStream_t s);               \
+                                   StageCoef c, int tx, int ty, int kp, void *fields,                  \
+                                   const long long *node_start, long long total_nodes, cudaStream_t s);\
     size_t batch_run_bytes(real *);                                                                    \
-    void batch_run_fill(real *, void *dst, const Geo &g, const Tab<real> &t, long long off, int ntx);  \
+    void batch_run_fill(real *, void *dst, const Geo &g, const Tab<real> &t, long long off,            \
+                        long long foff, int ntx);                                                      \
     cudaError_t launch_init(real *f, const double *n, const double *ux, const double *uy,              \
                             const double *T, const Geo &g, const Tab<double> &t, cudaStream_t s);       \
     cudaError_t launch_moments_out(const real *f, double *n, double *ux, double *uy, double *T,        \
