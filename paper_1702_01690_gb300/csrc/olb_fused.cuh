@@ -862,6 +862,54 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             }
         }
     };
+    // learned weights (FP32 instances): the face of item (k, slot, along_x,
+    // r, c), or none (valid false); every lane of the warp calls it together,
+    // from a single call site, since the warp evaluates the network of its 32
+    // stencils on the tensor pipe
+    float *const mlp_sc = (LEARNED && F32) ? const_cast<float *>(mlp) + MLP_SCRATCH_OFF + (tid >> 5) * MLP_WARP_SCRATCH : nullptr;
+    auto learned_face = [&](int k, int slot, bool along_x, int r, int c, bool valid) {
+        const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
+        valid = valid && (along_x ? (y0 + r < g.ny && x0 + c <= g.nx) : (x0 + c < g.nx && y0 + r <= g.ny));
+        // the stencil v0 .. v4 in the upwind orientation, as positions of the
+        // staged region: x faces along row 3 + r, y faces along column 4 + c
+        int p0 = 0, step = 1;
+        if (along_x) {
+            p0 = (k1 > 2) ? c + 1 : c + 6;
+            step = (k1 > 2) ? 1 : -1;
+        } else {
+            p0 = (k2 > 2) ? r : r + 5;
+            step = (k2 > 2) ? 1 : -1;
+        }
+        real d[4] = {0, 0, 0, 0}, v2 = 0;
+        if (valid) {
+            const real *P = &sm.pop[k][0][0];
+            auto at = [&](int m) { return along_x ? (3 + r) * HX + p0 + m * step : (p0 + m * step) * HX + 4 + c; };
+            if constexpr (F32) {
+                const float *Lo = &sm.pl.lo[k][0][0];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) d[m] = pdiff(P[at(m + 1)], Lo[at(m + 1)], P[at(m)], Lo[at(m)]);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) d[m] = P[at(m + 1)] - P[at(m)];
+                v2 = P[at(2)];
+            }
+        }
+        float x[MLP_IN], w[MLP_OUT] = {0.0f, 0.0f, 0.0f};
+        const bool acts = learned_input<real>(d[0], d[1], d[2], d[3], x);
+        // the whole warp skips the network when none of its stencils needs it
+        if (__any_sync(0xffffffffu, acts)) mlp_weights_warp(mlp, x, w, mlp_sc);
+        if (valid) {
+            real res;
+            if (acts) {
+                res = learned_combine<real>(w, d[0], d[1], d[2], d[3], v2);
+            } else {
+                const real q12 = d[1] * d[1], q23 = d[2] * d[2];
+                res = weno5_core(d[0], d[1], d[2], d[3], q23, real(2.5) * q12, real(2.5) * q23, v2);
+            }
+            if (along_x) sm.fx[slot][r][c] = res;
+            else sm.fy[slot][r][c] = res;
+        }
+    };
     // node update of velocity k (faces in slot) at tile node (tx_, ty_):
     // FP64 with Ek = E_q(k1), gyk = g_q(k2); FP32 with Ek = n ge(k1),
     // oxk = n go(k1), gyk = ge(k2), oyk = go(k2)
@@ -928,7 +976,41 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     };
     for (int kb = 0; kb < NK; kb += KF) {
         __syncthreads();  // loc ready / the previous velocities' faces are consumed
-        if constexpr (Sf::ALL_FACES && !LEARNED && sizeof(real) == 4) {
+        if constexpr (LEARNED && sizeof(real) == 4) {
+            // FP32 with learned weights: the network on the tensor pipe, one
+            // warp per 32 stencils (FP64 instances, bound by the FP64 pipe,
+            // evaluate it per thread in the loop further down: that measured
+            // faster there).  The faces of this pass (all 25 velocities' on small tiles, else
+            // those of velocities kb .. kb+KP-1), enumerated as below, on
+            // whole warps: items past the end take part in the network only
+            int end[KF], total = 0;
+#pragma unroll
+            for (int sub = 0; sub < KF; ++sub) {
+                const int k = kb + sub;
+                if (k < NK) total += (k / NQ != 2 ? nfx : 0) + (k % NQ != 2 ? nfy : 0);
+                end[sub] = total;
+            }
+            const int padded = (total + 31) & ~31;
+            for (int e = tid; e < padded; e += NT) {
+                int sub = 0, start = 0;
+#pragma unroll
+                for (int q = 0; q + 1 < KF; ++q)
+                    if (e >= end[q]) {
+                        sub = q + 1;
+                        start = end[q];
+                    }
+                const int k = kb + sub;
+                int f = e - start;
+                if (k / NQ == 2) f += nfx;
+                const bool valid = e < total && k < NK;
+                const bool along_x = f < nfx;
+                const int r = along_x ? f / (TX + 1) : (f - nfx) / TX;
+                const int c = along_x ? f - r * (TX + 1) : f - nfx - r * TX;
+                // one call site: the warp's network must run as one instruction
+                // stream (mma.sync needs every lane at the same instruction)
+                learned_face(k, sub, along_x, valid ? r : 0, valid ? c : 0, valid);
+            }
+        } else if constexpr (Sf::ALL_FACES && sizeof(real) == 4) {
             // FP32 (issue-bound): every face of every velocity once, in strips
             // of SX (SY) consecutive faces along a tile row (column), each
             // strip in the upwind direction of its velocity: the x strips of
@@ -1060,7 +1142,8 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
 }
 
 // Shared memory of the single-grid kernel: the tile staging, then (learned
-// weights only) the network's parameters at a 16-byte aligned offset.
+// weights only) the network's parameters at a 16-byte aligned offset and the
+// warps' scratch for the network's tensor-pipe layer.
 template <typename real, int TX, int TY, int KP>
 constexpr size_t mlp_offset()
 {
@@ -1069,27 +1152,34 @@ constexpr size_t mlp_offset()
 template <typename real, int TX, int TY, int KP, bool LEARNED>
 constexpr size_t fused_smem_bytes()
 {
-    return LEARNED ? mlp_offset<real, TX, TY, KP>() + (MLP_P + 1) * sizeof(float) : sizeof(FusedSmem<real, TX, TY, KP>);
+    // learned: the parameters; FP32 also the split W2 and MLP_WARP_SCRATCH
+    // floats per warp
+    constexpr size_t mlp_floats = sizeof(real) == 4
+                                      ? MLP_SCRATCH_OFF + FusedSmem<real, TX, TY, KP>::NT / 32 * MLP_WARP_SCRATCH
+                                      : MLP_P + 1;
+    return LEARNED ? mlp_offset<real, TX, TY, KP>() + mlp_floats * sizeof(float) : sizeof(FusedSmem<real, TX, TY, KP>);
 }
 
 // CTAs per SM that the register allocation must leave room for: as many as
 // the shared memory (228 KB per SM, 1 KB of it reserved per CTA) and the
 // 2048 threads of an SM allow.  Without this bound the compiler may take
 // more registers than that occupancy leaves (e.g. 80 for a 512-thread CTA
-// that could otherwise share its SM).  Learned-weight instances keep the
-// registers their network needs.
-constexpr int fused_min_ctas(size_t smem_bytes, int threads, bool learned = false)
+// that could otherwise share its SM), capped at cap when cap > 0.
+constexpr int fused_min_ctas(size_t smem_bytes, int threads, int cap = 0)
 {
     const int by_smem = (int)((228 * 1024) / (smem_bytes + 1024)), by_threads = 2048 / threads;
     const int n = by_smem < by_threads ? by_smem : by_threads;
-    return learned || n < 1 ? 1 : n;
+    return n < 1 ? 1 : (cap > 0 && n > cap ? cap : n);
 }
 
-// Single grid: one CTA per tile.
+// Single grid: one CTA per tile.  Learned-weight instances leave their
+// network the registers it needs: FP32 (tensor-pipe network) at most two CTAs
+// per SM, FP64 (per-thread network) one.
 template <typename real, int TX, int TY, int KP, bool LEARNED>
 __global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT,
                                   fused_min_ctas(fused_smem_bytes<real, TX, TY, KP, LEARNED>(),
-                                                 FusedSmem<real, TX, TY, KP>::NT, LEARNED))
+                                                 FusedSmem<real, TX, TY, KP>::NT,
+                                                 LEARNED ? (sizeof(real) == 4 ? 2 : 1) : 0))
 k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
         const __grid_constant__ Geo g, const __grid_constant__ Tab<real> t, real ca, real cb, real cc, real ca_lo,
         real cb_lo, const float *__restrict__ mlp, const __grid_constant__ TmaArg tma,
@@ -1102,6 +1192,10 @@ k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict_
     if constexpr (LEARNED) {
         mlp_sm = reinterpret_cast<float *>(smem_raw + mlp_offset<real, TX, TY, KP>());
         for (int p = threadIdx.x; p < MLP_P; p += blockDim.x) mlp_sm[p] = __ldg(mlp + p);
+        if constexpr (sizeof(real) == 4) {
+            __syncthreads();
+            mlp_split_w2(mlp_sm);
+        }
         // made visible by the first barrier inside stage_tile
     }
     stage_tile<real, TX, TY, KP, LEARNED>(sm, fs, fn, out, status, g, t, blockIdx.x * TX, blockIdx.y * TY, ca, cb, cc,

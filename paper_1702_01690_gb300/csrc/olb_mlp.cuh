@@ -145,4 +145,186 @@ __device__ __forceinline__ float weno5_learned_corr(const float *__restrict__ th
     return fmaf(w[0], G1, fmaf(w[1], G2, w[2] * G3));
 }
 
+// ---------------------------------------------------------------- the network on the tensor pipe
+// Inside the stage kernel the 32 lanes of a warp evaluate the network for 32
+// stencils at once: layer 1 per lane, the 32 x 32 layer as a matrix product
+// on the tensor pipe (mma.sync m16n8k8 with TF32 operands; each operand
+// split into a TF32 high part and a TF32 remainder and the product taken as
+// hi hi + hi lo + lo hi, accurate to ~2^-21 like an FP32 dot product), layer 3
+// and the softmax per stencil.
+
+// scratch floats per warp: one 16 x 8 block of layer-1 outputs (row stride 9)
+constexpr int MLP_WARP_SCRATCH = 16 * 9;
+// shared memory after the parameters (1348 floats): W2 split into TF32 high
+// parts and remainders (2 x 1024 words), then the warps' scratch
+constexpr int MLP_W2HI_OFF = 1348, MLP_W2LO_OFF = 1348 + 1024, MLP_SCRATCH_OFF = 1348 + 2048;
+
+__device__ __forceinline__ void tf32_split(float v, unsigned &hi, unsigned &lo)
+{
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(v));
+    const float r = v - __uint_as_float(hi);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
+// Fill the split copies of W2 after the parameters (all threads of the CTA).
+__device__ __forceinline__ void mlp_split_w2(float *th)
+{
+    unsigned *w2h = reinterpret_cast<unsigned *>(th + MLP_W2HI_OFF);
+    unsigned *w2l = reinterpret_cast<unsigned *>(th + MLP_W2LO_OFF);
+    for (int i = threadIdx.x; i < MLP_H * MLP_H; i += blockDim.x) tf32_split(th[MLP_W2 + i], w2h[i], w2l[i]);
+}
+
+// c += a b for one m16n8k8 tile (row-major A, column-major B, FP32 accumulators).
+__device__ __forceinline__ void mma_tf32(float c[4], const unsigned a[4], const unsigned b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Weights w of this lane's stencil x; every lane of the warp must call it,
+// from one call site (mma.sync.aligned needs the whole warp at the same
+// instruction; lanes whose stencil the network does not act on pass any x and
+// ignore w).
+// th: parameters in shared memory; sc: this warp's MLP_WARP_SCRATCH floats.
+__device__ __forceinline__ void mlp_weights_warp(const float *__restrict__ th, const float x[MLP_IN],
+                                                 float w[MLP_OUT], float *sc)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    // layer 2 accumulators: rows = stencils (lanes), 16 per m-tile mt;
+    // columns = outputs, 8 per n-tile nt; k = the 32 layer-1 outputs, 8 per
+    // step ks, each step's layer-1 outputs computed just before it
+    float acc[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.0f;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+        float hc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = 8 * ks + q;
+            float a = th[MLP_B1 + j];
+#pragma unroll
+            for (int i = 0; i < MLP_IN; ++i) a = fmaf(th[MLP_W1 + j * MLP_IN + i], x[i], a);
+            hc[q] = tanh_fast(a);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            // the m-tile's 16 lanes put their 8 layer-1 outputs in the scratch
+            __syncwarp();
+            if ((lane >> 4) == mt)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) sc[(lane & 15) * 9 + q] = hc[q];
+            __syncwarp();
+            unsigned ah[4], al[4];
+            tf32_split(sc[g * 9 + t], ah[0], al[0]);
+            tf32_split(sc[(g + 8) * 9 + t], ah[1], al[1]);
+            tf32_split(sc[g * 9 + t + 4], ah[2], al[2]);
+            tf32_split(sc[(g + 8) * 9 + t + 4], ah[3], al[3]);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                // B[k][n] = W2[n][k]: k = 8 ks + t (+4), n = 8 nt + g
+                const unsigned *w2h = reinterpret_cast<const unsigned *>(th + MLP_W2HI_OFF);
+                const unsigned *w2l = reinterpret_cast<const unsigned *>(th + MLP_W2LO_OFF);
+                const int i0 = (8 * nt + g) * MLP_H + 8 * ks + t;
+                const unsigned bh[2] = {w2h[i0], w2h[i0 + 4]}, bl[2] = {w2l[i0], w2l[i0 + 4]};
+                mma_tf32(acc[mt][nt], al, bh);
+                mma_tf32(acc[mt][nt], ah, bl);
+                mma_tf32(acc[mt][nt], ah, bh);
+            }
+        }
+    }
+    // h2 = tanh(acc + b2) and layer 3: accumulator q of (mt, nt) holds stencil
+    // 16 mt + g + 8 (q >> 1) = g + 8 m, output 8 nt + 2 t + (q & 1)
+    float z[4][MLP_OUT];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int o = 0; o < MLP_OUT; ++o) z[m][o] = 0.0f;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 8 * nt + 2 * t + (q & 1), m = 2 * mt + (q >> 1);
+                const float h2 = tanh_fast(acc[mt][nt][q] + th[MLP_B2 + j]);
+#pragma unroll
+                for (int o = 0; o < MLP_OUT; ++o) z[m][o] = fmaf(th[MLP_W3 + o * MLP_H + j], h2, z[m][o]);
+            }
+    // sum over the four lanes of a row group (t = 0..3): every one gets the total
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int o = 0; o < MLP_OUT; ++o) {
+            z[m][o] += __shfl_xor_sync(0xffffffffu, z[m][o], 1);
+            z[m][o] += __shfl_xor_sync(0xffffffffu, z[m][o], 2);
+        }
+    // lane (g, t) finishes stencil g + 8 t
+    float zz[MLP_OUT];
+#pragma unroll
+    for (int o = 0; o < MLP_OUT; ++o) {
+        float v = z[0][o];
+        v = t == 1 ? z[1][o] : v;
+        v = t == 2 ? z[2][o] : v;
+        v = t == 3 ? z[3][o] : v;
+        zz[o] = v + th[MLP_B3 + o];
+    }
+    const float zm = fmaxf(zz[0], fmaxf(zz[1], zz[2]));
+    const float e0 = expf(zz[0] - zm), e1 = expf(zz[1] - zm), e2 = expf(zz[2] - zm);
+    const float inv = 1.0f / (e0 + e1 + e2);
+    // stencil F sits in lane F; lane 4 (F mod 8) + F / 8 finished it
+    const int src = 4 * (lane & 7) + (lane >> 3);
+    w[0] = __shfl_sync(0xffffffffu, e0 * inv, src);
+    w[1] = __shfl_sync(0xffffffffu, e1 * inv, src);
+    w[2] = __shfl_sync(0xffffffffu, e2 * inv, src);
+}
+
+// The learned interface value from the stencil's first differences d01 ..
+// d34 (and, in FP64, its upwind node v2): whether the network acts (no
+// vanishing indicator, min sigma_q < MLP_GUARD max sigma_q) and its
+// normalised input x (shift invariant: the stencil relative to v0).
+template <typename real>
+__device__ __forceinline__ bool learned_input(real d01, real d12, real d23, real d34, float x[MLP_IN])
+{
+    const real a1 = d12 - d01, b1 = fma(real(3), d12, -d01);
+    const real a2 = d23 - d12, b2 = d12 + d23;
+    const real a3 = d34 - d23, b3 = fma(real(-3), d23, d34);
+    const real s1 = fma(real(13) * a1, a1, real(3) * b1 * b1);
+    const real s2 = fma(real(13) * a2, a2, real(3) * b2 * b2);
+    const real s3 = fma(real(13) * a3, a3, real(3) * b3 * b3);
+    const real smin = s1 < s2 ? (s1 < s3 ? s1 : s3) : (s2 < s3 ? s2 : s3);
+    const real smax = s1 > s2 ? (s1 > s3 ? s1 : s3) : (s2 > s3 ? s2 : s3);
+    const bool zero = (a1 == real(0) && b1 == real(0)) || (a2 == real(0) && b2 == real(0)) ||
+                      (a3 == real(0) && b3 == real(0));
+    const bool acts = !zero && smin < real(MLP_GUARD) * smax;
+    const real w1 = d01, w2 = w1 + d12, w3 = w2 + d23, w4 = w3 + d34;
+    const real mx = fmax(fmax(real(0), w1), fmax(fmax(w2, w3), w4));
+    const real mn = fmin(fmin(real(0), w1), fmin(fmin(w2, w3), w4));
+    const real mean = (((w1 + w2) + w3) + w4) * real(0.2);
+    const real ir = acts ? real(1) / (mx - mn) : real(0);
+    x[0] = (float)((real(0) - mean) * ir);
+    x[1] = (float)((w1 - mean) * ir);
+    x[2] = (float)((w2 - mean) * ir);
+    x[3] = (float)((w3 - mean) * ir);
+    x[4] = (float)((w4 - mean) * ir);
+    return acts;
+}
+
+// v2 + sum_q w_q (Fhat^q - v2) (Eq. weno5_flux) from first differences.
+template <typename real>
+__device__ __forceinline__ real learned_combine(const float w[MLP_OUT], real d01, real d12, real d23, real d34,
+                                                real v2)
+{
+    const real G1 = fma(real(5.0 / 6.0), d12, real(-1.0 / 3.0) * d01);
+    const real G2 = fma(real(1.0 / 3.0), d23, real(1.0 / 6.0) * d12);
+    const real G3 = fma(real(2.0 / 3.0), d23, real(-1.0 / 6.0) * d34);
+    return fma((real)w[0], G1, fma((real)w[1], G2, fma((real)w[2], G3, v2)));
+}
+
 }  // namespace olb
