@@ -10,9 +10,10 @@ GPU, each with its own stage time and roofline fraction:
   learned_fp64  learned WENO weights (network in FP32, populations FP64)
   learned_fp32  learned WENO weights with the FP32 path
   batch_fp64/32 64 independent runs of uneven size (32^2 .. 1024^2, 13.5 M
-                nodes) in one persistent launch per stage, autotuned shape
-A "step" is one full RK-3 step (three launches of the fused stage kernel:
-moments, force, WENO-5 fluxes, collision and RK combination) of the whole grid.
+                nodes) in one launch per stage, autotuned shape
+A "step" is one full RK-3 step of the whole grid: three stages, each the
+per-node moments pre-pass and the fused stage kernel (force, WENO-5 fluxes,
+collision and RK combination), six launches in all.
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
 on the context's stream, with a 256 MiB buffer written between steps (the
@@ -541,8 +542,9 @@ def oracle_leg(args, p, fields, dev_fields, theta, stream):
 def run_batch_legs(args, world, stream, peak64, peak32):
     """64 independent runs of uneven sizes (32^2 .. 1024^2 shear and
     longitudinal waves, Laplace drops, planar wall runs; 13.5 M nodes) in one
-    persistent launch per stage, replayed from CUDA graphs, shape autotuned.
-    The working set (3 x 25 x 13.5 M values) is far larger than L2."""
+    launch per stage (one CTA per tile of every run), replayed from CUDA
+    graphs, shape autotuned.  The working set (3 x 25 x 13.5 M values) is far
+    larger than L2."""
     import torch
     from paper_1702_01690_gb300 import inputs, olb
     runs = inputs.batch_sweep()

@@ -228,8 +228,8 @@ int olb_get_tile(olb_ctx *ctx, int *tx, int *ty, int *kp);
 
 /* ------------------------------------------------------------------------
  * Batches: many independent runs (uneven grid sizes, each with its own
- * olb_params) advanced together, one persistent launch per RK-3 stage that
- * strides over all (run, tile) work items, replayed from CUDA graphs.  Not
+ * olb_params) advanced together, one launch per RK-3 stage with one CTA per
+ * (run, tile) work item, replayed from CUDA graphs.  Not
  * part of the paper: it serves parameter sweeps (ds, T_w, drop radius) whose
  * single grids are too small to fill the GPU.  All runs must share the
  * precision.  Conventions as for single contexts; `run` indexes the array

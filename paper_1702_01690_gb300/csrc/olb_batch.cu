@@ -1,12 +1,14 @@
 // olb_batch.cu -- many independent runs (uneven grids, own parameters) in one
-// persistent launch per RK-3 stage, replayed from CUDA graphs, with an
-// autotuner that times the compiled stage shapes.
+// launch per RK-3 stage (one CTA per tile of every run), replayed from CUDA
+// graphs, with an autotuner that times the compiled stage shapes.
 //
 // Device layout: the populations of all runs share three buffers (f^n, f^(1),
 // f^(2)); run r occupies 25 x ny_r x pitch_r values at offset off_r of each.
 // A descriptor per run (geometry, velocity and wall tables, offset, tiles per
-// row) and the prefix sum of tiles per run drive the persistent kernel
-// (k_fused_batch in olb_fused.cuh); each run has its own status word.
+// row) and the prefix sum of tiles per run drive the stage kernel
+// (k_fused_batch in olb_fused.cuh); each run has its own status word.  Where
+// the tile shape suits TMA, each run also has a tensor map per buffer
+// ([3][count], in device memory): tiles inside a run are staged by one copy.
 #include <cmath>
 #include <algorithm>
 #include <cstring>
@@ -51,6 +53,8 @@ struct olb_batch {
     long long *node_start = nullptr;     // [count + 1] prefix sum of the runs' node counts
     long long total_nodes = 0;
     long long max_nodes = 0;
+    TmaMap *tmaps = nullptr;             // [3][count] tensor maps (runs x buffers) for the current shape
+    bool tma_ok = false;                 // every map encoded
     int tx = 16, ty = 8, kp = 2, total_tiles = 0;
     std::vector<char> init;
     cudaStream_t cap = nullptr;
@@ -97,9 +101,19 @@ static cudaError_t batch_upload(olb_batch *b)
     }
     start[b->count] = acc;
     b->total_tiles = acc;
+    // tensor maps of every run in every buffer; if one cannot be encoded
+    // (shape unsuited to TMA, or no driver entry point) no run uses TMA
+    std::vector<TmaMap> maps((size_t)3 * b->count);
+    b->tma_ok = true;
+    for (int k = 0; k < 3 && b->tma_ok; ++k)
+        for (int r = 0; r < b->count && b->tma_ok; ++r)
+            b->tma_ok = tma_encode(&maps[(size_t)k * b->count + r], (const char *)b->f[k] + b->off[r] * b->elt,
+                                   b_fp64(b), b->geo[r], b->tx, b->ty);
     cudaError_t e = cudaMemcpyAsync(b->runs, host.data(), host.size(), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->tile_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && b->tma_ok)
+        e = cudaMemcpyAsync(b->tmaps, maps.data(), maps.size() * sizeof(TmaMap), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     return e;
 }
@@ -110,6 +124,11 @@ static cudaError_t batch_prepare(olb_batch *b)
                      : prepare_fused((float *)nullptr, b->tx, b->ty, b->kp, false);
 }
 
+// The velocity tables (identical in every run's Tab; only the wall entries
+// differ, and the kernel reads those from each run's descriptor).
+static const Tab<double> &batch_tab(const olb_batch *b, double *) { return b->tab64[0]; }
+static const Tab<float> &batch_tab(const olb_batch *b, float *) { return b->tab32[0]; }
+
 template <typename real>
 static cudaError_t batch_stage(olb_batch *b, int st, cudaStream_t s)
 {
@@ -118,8 +137,11 @@ static cudaError_t batch_stage(olb_batch *b, int st, cudaStream_t s)
     real *dst[3] = {f1, f2, f0};
     // the dt-proportional coefficient is multiplied by each run's own dt
     const StageCoef coef[3] = {{0.0, 1.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}};
+    // src[st] is buffer st: its maps are row st of tmaps
+    const TmaMap *maps = b->tma_ok ? b->tmaps + (size_t)st * b->count : nullptr;
     return launch_fused_batch(src[st], f0, dst[st], b->status, b->runs, b->tile_start, b->count, b->total_tiles,
-                              coef[st], b->tx, b->ty, b->kp, b->fields, b->node_start, b->total_nodes, s);
+                              batch_tab(b, (real *)nullptr), coef[st], b->tx, b->ty, b->kp, b->fields, b->node_start,
+                              b->total_nodes, maps, s);
 }
 
 static cudaError_t batch_enqueue_steps(olb_batch *b, int n, cudaStream_t s)
@@ -158,6 +180,7 @@ static void batch_free(olb_batch *b)
     cudaFree(b->stage4);
     cudaFree(b->fields);
     cudaFree(b->node_start);
+    cudaFree(b->tmaps);
 }
 
 static bool batch_shape_index(int tx, int ty, int kp, int *k)
@@ -247,6 +270,7 @@ extern "C" int olb_batch_create(const olb_params *runs, int count, void *stream,
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->stage4, (size_t)4 * b->max_nodes * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&b->fields, (size_t)facc);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->node_start, (size_t)(count + 1) * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->tmaps, (size_t)3 * count * sizeof(TmaMap));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->node_start, nstart.data(), (size_t)(count + 1) * sizeof(long long),
                             cudaMemcpyHostToDevice, b->stream);

@@ -358,7 +358,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity)
 // staging arrays (pop, then the lo planes in FP32, contiguous in FusedSmem in
 // the box's order), completion tracked by an mbarrier.  If the bounded wait
 // runs out, bit 1 of the status word is set, the copy is waited for once more
-// (bounded) and false is returned: the caller leaves the tile untouched.
+// (bounded) and false is returned: the caller leaves the tile untouched and
+// the CTA stops.  After a completed copy the barrier is invalidated, so that
+// a CTA that stages several tiles initialises it afresh for each.
 template <typename real, int TX, int TY, int KP>
 __device__ __forceinline__ bool tma_stage(FusedSmem<real, TX, TY, KP> &sm, const TmaMap *tmap, int gx0, int gy0,
                                           int *status)
@@ -384,6 +386,8 @@ __device__ __forceinline__ bool tma_stage(FusedSmem<real, TX, TY, KP> &sm, const
         mbar_wait(mbar, 0);
         return false;
     }
+    // every thread has passed its wait (the barrier above)
+    if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mbar) : "memory");
     return true;
 }
 
@@ -392,13 +396,18 @@ __device__ __forceinline__ bool tma_stage(FusedSmem<real, TX, TY, KP> &sm, const
 // f^n, f_s and dt L (Eq. rk3), in the population precision; ca_lo, cb_lo:
 // their remainders (FP32: 1/3 and 2/3 as double-float constants; 0 in FP64).
 // g and t may live in parameter space (single grid) or shared memory
-// (batch); mlp: the learned network's parameters in shared memory (LEARNED
-// only); tmap: TMA map of fs for this tile shape (single grids), or nullptr;
-// fields: the moments of fs from k_fields, or nullptr to compute them here.
+// (batch); tw: the table of the wall entries (geqw, inv_den), t itself for
+// a single grid, the run's own in a batch, whose velocity tables t are common
+// to all runs and passed as a kernel parameter; mlp: the learned network's
+// parameters in shared memory (LEARNED
+// only); tmap: TMA map of fs (of this run, in a batch) for this tile shape,
+// or nullptr; fields: the moments of fs from k_fields, or nullptr to compute
+// them here.  Returns false when the TMA copy timed out (the CTA must stop).
 template <typename real, int TX, int TY, int KP, bool LEARNED = false>
-__device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, const real *__restrict__ fs,
+__device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, const real *__restrict__ fs,
                                            const real *fn, real *out, int *__restrict__ status, const Geo &g,
-                                           const Tab<real> &t, const int x0, const int y0, const real ca,
+                                           const Tab<real> &t, const Tab<real> &tw, const int x0, const int y0,
+                                           const real ca,
                                            const real cb, const real cc, const real ca_lo, const real cb_lo,
                                            const float *mlp = nullptr, const TmaMap *tmap = nullptr,
                                            const StageFields<real> *fields = nullptr)
@@ -421,7 +430,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     //    set in phase 3; anything further out is never read and holds 0.
     const bool inside = tmap != nullptr && x0 >= 4 && x0 + TX + 4 <= g.nx && y0 >= 3 && y0 + TY + 3 <= g.ny;
     if (inside) {
-        if (!tma_stage(sm, tmap, x0 - 4, y0 - 3, status)) return;
+        if (!tma_stage(sm, tmap, x0 - 4, y0 - 3, status)) return false;
     } else {
         for (int e = tid; e < HY * HX; e += NT) {
             const int r = e / HX, c = e - r * HX;
@@ -592,7 +601,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
         const unsigned half = (tid & 16) ? 0xffff0000u : 0x0000ffffu;
 #pragma unroll
         for (int o = 8; o > 0; o >>= 1) wf += __shfl_xor_sync(half, wf, o);
-        if (v == 0) sm.wnw[side][tr] = -wf * t.inv_den[side];
+        if (v == 0) sm.wnw[side][tr] = -wf * tw.inv_den[side];
     }
 
     // ---- 3. sides: n and Delta p reflected evenly into the ghost layers of
@@ -636,7 +645,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 const int c = side ? g.nx + m - (x0 - 4) : -1 - m - (x0 - 4);
                 if (c < 0 || c >= HX) continue;
                 const int k = NQ * (side ? v / 5 : 3 + v / 5) + v % 5;
-                sm.pop[k][tr + 3][c] = sm.wnw[side][tr] * t.geqw[side][k];
+                sm.pop[k][tr + 3][c] = sm.wnw[side][tr] * tw.geqw[side][k];
                 if constexpr (sizeof(real) == 4) sm.pl.lo[k][tr + 3][c] = 0.0f;
             }
         }
@@ -1139,6 +1148,7 @@ __device__ __forceinline__ void stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             }
         }
     }
+    return true;
 }
 
 // Shared memory of the single-grid kernel: the tile staging, then (learned
@@ -1198,16 +1208,18 @@ k_fused(const real *__restrict__ fs, const real *fn, real *out, int *__restrict_
         }
         // made visible by the first barrier inside stage_tile
     }
-    stage_tile<real, TX, TY, KP, LEARNED>(sm, fs, fn, out, status, g, t, blockIdx.x * TX, blockIdx.y * TY, ca, cb, cc,
-                                          ca_lo, cb_lo, mlp_sm, tma.on ? &tma.map : nullptr,
+    stage_tile<real, TX, TY, KP, LEARNED>(sm, fs, fn, out, status, g, t, t, blockIdx.x * TX, blockIdx.y * TY, ca, cb,
+                                          cc, ca_lo, cb_lo, mlp_sm, tma.on ? &tma.map : nullptr,
                                           fields.n ? &fields : nullptr);
 }
 
-// Batch of independent runs (uneven grid sizes, own parameters): a
-// persistent grid strides over the (run, tile) work items; tile_start[r] is
-// the first item of run r (prefix sum, tile_start[nruns] = total).  Each run
-// has its populations at offset `off` of the three shared buffers and its own
-// status word.
+// Batch of independent runs (uneven grid sizes, own parameters): one CTA per
+// (run, tile) work item, in the order of the items, so that the hardware
+// dispatches neighbouring tiles together and their halos stay in L2 (a
+// persistent grid-stride loop let the CTAs drift apart and measured slower);
+// tile_start[r] is the first item of run r (prefix sum, tile_start[nruns] =
+// total).  Each run has its populations at offset `off` of the three shared
+// buffers and its own status word.
 // 16-byte aligned and sized: the kernel copies one descriptor into shared
 // memory with 16-byte loads, so consecutive array elements must stay aligned
 // and the whole struct must be covered by whole int4 words.
@@ -1232,34 +1244,38 @@ __global__ void __launch_bounds__(FusedSmem<real, TX, TY, KP>::NT,
                                       : (fused_min_ctas(sizeof(FusedSmem<real, TX, TY, KP>) + sizeof(BatchRun<real>),
                                                         FusedSmem<real, TX, TY, KP>::NT) > 1 ? 2 : 1))
 k_fused_batch(const real *__restrict__ fs, const real *fn, real *out, int *__restrict__ status,
-              const BatchRun<real> *__restrict__ runs, const int *__restrict__ tile_start, int nruns, int total,
-              real ca, real cb, real ccoef, real ca_lo, real cb_lo, char *fields)
+              const BatchRun<real> *__restrict__ runs, const int *__restrict__ tile_start, int nruns,
+              const __grid_constant__ Tab<real> tv, real ca, real cb, real ccoef, real ca_lo, real cb_lo,
+              char *fields, const TmaMap *__restrict__ tmaps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<FusedSmem<real, TX, TY, KP> *>(smem_raw);
     __shared__ __align__(16) BatchRun<real> run;
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        int lo = 0, hi = nruns - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(tile_start + mid) <= item) lo = mid;
-            else hi = mid - 1;
-        }
-        {
-            const int4 *src = reinterpret_cast<const int4 *>(runs + lo);
-            int4 *dst = reinterpret_cast<int4 *>(&run);
-            for (int w = threadIdx.x; w < (int)(sizeof(BatchRun<real>) / sizeof(int4)); w += blockDim.x)
-                dst[w] = __ldg(src + w);
-        }
-        __syncthreads();
-        const int lt = item - __ldg(tile_start + lo);
-        const int x0 = (lt % run.ntx) * TX, y0 = (lt / run.ntx) * TY;
-        const StageFields<real> fl = fields ? fields_of<real>(fields + run.foff, run.g) : StageFields<real>{};
-        stage_tile<real, TX, TY, KP>(sm, fs + run.off, fn + run.off, out + run.off, status + lo, run.g, run.t, x0, y0,
-                                     ca, cb, ccoef * (real)run.g.dt, ca_lo, cb_lo, nullptr, nullptr,
-                                     fields ? &fl : nullptr);
-        __syncthreads();  // the next item overwrites the shared staging
+    const int item = blockIdx.x;
+    int lo = 0, hi = nruns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_start + mid) <= item) lo = mid;
+        else hi = mid - 1;
     }
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(runs + lo);
+        int4 *dst = reinterpret_cast<int4 *>(&run);
+        for (int w = threadIdx.x; w < (int)(sizeof(BatchRun<real>) / sizeof(int4)); w += blockDim.x)
+            dst[w] = __ldg(src + w);
+    }
+    __syncthreads();
+    const int lt = item - __ldg(tile_start + lo);
+    const int x0 = (lt % run.ntx) * TX, y0 = (lt / run.ntx) * TY;
+    const StageFields<real> fl = fields ? fields_of<real>(fields + run.foff, run.g) : StageFields<real>{};
+    // the run's tensor map of fs lives in global memory, written by the host
+    // before the launch: acquire it for the tensormap proxy before the thread
+    // that issues the copy uses it
+    const TmaMap *tm = tmaps ? tmaps + lo : nullptr;
+    if (tm && threadIdx.x == 0)
+        asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(tm) : "memory");
+    stage_tile<real, TX, TY, KP>(sm, fs + run.off, fn + run.off, out + run.off, status + lo, run.g, tv, run.t, x0, y0,
+                                 ca, cb, ccoef * (real)run.g.dt, ca_lo, cb_lo, nullptr, tm, fields ? &fl : nullptr);
 }
 
 // The moments pre-pass for a batch: one thread per node of every run (a
@@ -1340,32 +1356,24 @@ cudaError_t fused_launch_one(const real *fs, const real *fn, real *out, int *sta
 
 template <typename real, int TX, int TY, int KP>
 cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, int *status, const void *runs,
-                                   const int *tile_start, int nruns, int total, StageCoef c, void *fields,
-                                   const long long *node_start, long long total_nodes, cudaStream_t s)
+                                   const int *tile_start, int nruns, int total, const Tab<real> &t, StageCoef c,
+                                   void *fields, const long long *node_start, long long total_nodes,
+                                   const TmaMap *tmaps, cudaStream_t s)
 {
-    static int ctas_per_sm[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int &per = ctas_per_sm[dev & 63];
-    if (per == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per, k_fused_batch<real, TX, TY, KP>, FusedSmem<real, TX, TY, KP>::NT, sizeof(FusedSmem<real, TX, TY, KP>));
-        if (e != cudaSuccess || per < 1) per = 1;
-    }
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = total < per * sms ? total : per * sms;
-    if (grid < 1) return cudaSuccess;
+    if (total < 1) return cudaSuccess;
     if (fields && total_nodes > 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const long long want = (total_nodes + 255) / 256, cap = 8LL * sms * 8;
         k_fields_batch<real><<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(
             fs, static_cast<char *>(fields), static_cast<const BatchRun<real> *>(runs), node_start, nruns, total_nodes,
             status);
     }
-    k_fused_batch<real, TX, TY, KP><<<grid, FusedSmem<real, TX, TY, KP>::NT, sizeof(FusedSmem<real, TX, TY, KP>), s>>>(
-        fs, fn, out, status, static_cast<const BatchRun<real> *>(runs), tile_start, nruns, total, (real)c.ca,
-        (real)c.cb, (real)c.cc, (real)(c.ca - (double)(real)c.ca), (real)(c.cb - (double)(real)c.cb),
-        static_cast<char *>(fields));
+    k_fused_batch<real, TX, TY, KP><<<total, FusedSmem<real, TX, TY, KP>::NT, sizeof(FusedSmem<real, TX, TY, KP>), s>>>(
+        fs, fn, out, status, static_cast<const BatchRun<real> *>(runs), tile_start, nruns, t, (real)c.ca, (real)c.cb,
+        (real)c.cc, (real)(c.ca - (double)(real)c.ca), (real)(c.cb - (double)(real)c.cb), static_cast<char *>(fields),
+        tmaps);
     return cudaGetLastError();
 }
 
@@ -1389,8 +1397,8 @@ cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, in
         return fused_launch_one<real, A, B, C, true>(fs, fn, out, status, g, t, c, mlp, tma, fields, s);
 #define OLB_FUSED_BATCH_CASE(real, A, B, C)                                                                  \
     if (tx == A && ty == B && kp == C)                                                                       \
-        return fused_batch_launch_one<real, A, B, C>(fs, fn, out, status, runs, tile_start, nruns, total, c,     \
-                                                     fields, node_start, total_nodes, s);
+        return fused_batch_launch_one<real, A, B, C>(fs, fn, out, status, runs, tile_start, nruns, total, t,     \
+                                                     c, fields, node_start, total_nodes, tmaps, s);
 #define OLB_DEFINE_FUSED(real)                                                                                \
     cudaError_t prepare_fused(real *, int tx, int ty, int kp, bool learned)                                   \
     {                                                                                                         \
@@ -1407,8 +1415,9 @@ cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, in
         return cudaErrorInvalidValue;                                                                         \
     }                                                                                                         \
     cudaError_t launch_fused_batch(const real *fs, const real *fn, real *out, int *status, const void *runs,  \
-                                   const int *tile_start, int nruns, int total, StageCoef c, int tx, int ty,  \
-                                   int kp, void *fields, const long long *node_start, long long total_nodes,  \
+                                   const int *tile_start, int nruns, int total, const Tab<real> &t,         \
+                                   StageCoef c, int tx, int ty, int kp, void *fields,                         \
+                                   const long long *node_start, long long total_nodes, const TmaMap *tmaps,   \
                                    cudaStream_t s)                                                            \
     {                                                                                                         \
         OLB_FUSED_SHAPE_CASES(real, OLB_FUSED_BATCH_CASE)                                                     \

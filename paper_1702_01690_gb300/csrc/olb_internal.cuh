@@ -104,8 +104,10 @@ struct StageCoef {
                              const float *mlp, const TmaMap *tma, void *fields, cudaStream_t s);       \
     cudaError_t launch_fused_batch(const real *fs, const real *fn, real *out, int *status,             \
                                    const void *runs, const int *tile_start, int nruns, int total,      \
-                                   StageCoef c, int tx, int ty, int kp, void *fields,                  \
-                                   const long long *node_start, long long total_nodes, cudaStream_t s);\
+                                   const Tab<real> &t, StageCoef c, int tx, int ty, int kp,            \
+                                   void *fields,                                                       \
+                                   const long long *node_start, long long total_nodes,                 \
+                                   const TmaMap *tmaps, cudaStream_t s);                               \
     size_t batch_run_bytes(real *);                                                                    \
     void batch_run_fill(real *, void *dst, const Geo &g, const Tab<real> &t, long long off,            \
                         long long foff, int ntx);                                                      \

@@ -1,4 +1,4 @@
-"""Batched runs (one persistent launch per stage over many grids) against the
+"""Batched runs (one launch per stage over the tiles of many grids) against the
 single-grid path and the oracle, and the autotuner."""
 import numpy as np
 import pytest
@@ -47,6 +47,37 @@ def test_batch_matches_single_contexts(olb, precision):
         ctx = olb.create(p, precision)
         ctx.init_fields(*fl)
         ctx.step(5)
+        if precision == 0:
+            assert np.array_equal(b.get_populations(r), ctx.get_populations()), r
+        else:
+            assert field_rel(b.get_populations(r), ctx.get_populations()) < 1e-6, r
+        ctx.close()
+    rc, per = b.status()
+    assert rc == 0 and not per.any()
+
+
+@pytest.mark.parametrize("precision,shape", [(0, (8, 8, 4)), (0, (16, 8, 2)), (1, (8, 8, 8)), (1, (32, 16, 1))])
+def test_batch_tma_tiles_match_single_contexts(olb, precision, shape):
+    """Runs large enough that most tiles lie inside their run (staged by one
+    TMA copy from the run's own tensor map, the maps of the two runs side by
+    side in device memory); walls on one run, periodic on the other."""
+    runs = []
+    for nx, ny, side in ((256, 256, 0), (200, 120, 1)):
+        ds = 1.0 / nx
+        p = inputs.RunParams(nx=nx, ny=ny, ds=ds, dt=0.25 * ds / inputs.P_MAX, tau=0.01,
+                             Tw=(0.85, 0.9), uw=(0.0, 0.01), side_x=side)
+        n, ux, uy, T = inputs.noisy_rest(nx, ny, 7 + nx, 1.0, 0.03, 0.95)
+        runs.append((p, (n, 0.01 * np.sin(np.arange(nx) / 9.0)[None, :] + 0 * n, uy, T)))
+    b = olb.Batch([p for p, _ in runs], precision)
+    b.set_tile(*shape)
+    for r, (p, fl) in enumerate(runs):
+        b.init_fields(r, *fl)
+    assert b.step(3) == 0
+    for r, (p, fl) in enumerate(runs):
+        ctx = olb.create(p, precision)
+        ctx.set_tile(*shape)
+        ctx.init_fields(*fl)
+        ctx.step(3)
         if precision == 0:
             assert np.array_equal(b.get_populations(r), ctx.get_populations()), r
         else:
