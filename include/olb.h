@@ -334,8 +334,7 @@ int olb_set_weno_mlp(olb_ctx *ctx, const float *theta);
  * file-scope device array of 2 * 25 * OLB_STATIC_MAX_NODES doubles (6.6 MB)
  * that every GPU which loads the library keeps until the process exits.  The
  * first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  All
- * calls share the array and it keeps the last call's contents (the status
+ * device current).  All calls share the array and it keeps the last call's contents (the status
  * word is cleared by each call): calls that overlap on the GPU -- on two
  * streams, or from two threads -- race and give wrong results. */
 int olb_step_static(const olb_params *p, void *stream, double *f, int nsteps);

@@ -1,6 +1,6 @@
-// olb_fp32.cu -- FP32 instances of the stage kernel (populations, fluxes and
-// stencils in FP32; Kahan-compensated moment sums; T and Delta p recovered
-// in FP64) and of the initialisation / output kernels.
+// olb_fp32.cu -- FP32 instances of the stage kernel (FP32 arithmetic on
+// populations stored as hi + lo pairs of floats; moments, T and Delta p in
+// double-float arithmetic) and of the initialisation / output kernels.
 #include "olb_fused.cuh"
 
 namespace olb {

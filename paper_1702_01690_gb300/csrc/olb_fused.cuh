@@ -429,6 +429,33 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     //    velocity component reversed (Sec. 3.4.1); diffuse-wall ghosts are
     //    set in phase 3; anything further out is never read and holds 0.
     const bool inside = tmap != nullptr && x0 >= 4 && x0 + TX + 4 <= g.nx && y0 >= 3 && y0 + TY + 3 <= g.ny;
+    // the pre-pass fields of this thread's first moment position (phase 2's
+    // item e = tid) are fetched into registers now, so that their latency
+    // overlaps the staging of the populations
+    using fld = typename S::fld;
+    fld pf_n{}, pf_dp{}, pf_T{}, pf_E{};
+    real pf_ux = 0, pf_uy = 0;
+    bool pf_ok = false, pf_node = false;
+    int pf_r = 0, pf_c = 0;
+    if (fields != nullptr && tid < HY * (HX - 2)) {
+        pf_r = tid / (HX - 2);
+        pf_c = tid - pf_r * (HX - 2) + 1;
+        const int gx = x0 - 4 + pf_c, gyr = y0 - 3 + pf_r;
+        pf_ok = !(g.walls && (gx < 0 || gx >= g.nx)) && !(g.spec_y && (gyr < 0 || gyr >= g.ny));
+        if (pf_ok) {
+            const long long o = (long long)wrap(gyr, g.ny) * g.pitch + wrap(gx, g.nx);
+            pf_n = fields->n[o];
+            pf_dp = fields->dp[o];
+            const int tr = pf_r - 3, tc = pf_c - 4;
+            pf_node = tr >= 0 && tr < TY && tc >= 0 && tc < TX;
+            if (pf_node) {
+                pf_ux = fields->ux[o];
+                pf_uy = fields->uy[o];
+                pf_T = fields->T[o];
+                if constexpr (sizeof(real) == 4) pf_E = fields->E[o];
+            }
+        }
+    }
     if (inside) {
         if (!tma_stage(sm, tmap, x0 - 4, y0 - 3, status)) return false;
     } else {
@@ -504,8 +531,19 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     const int nflux = ((int)left_wall + (int)right_wall) * TY * 16;
     if (fields != nullptr) {
         // moments from the per-node pre-pass (k_fields): n and Delta p on the
-        // region, u, T (FP32: and e) at the tile nodes
-        for (int e = tid; e < HY * (HX - 2); e += NT) {
+        // region, u, T (FP32: and e) at the tile nodes; item tid was fetched
+        // before phase 1
+        if (pf_ok) {
+            sm.n[pf_r][pf_c] = pf_n;
+            sm.dp[pf_r][pf_c] = pf_dp;
+            if (pf_node) {
+                sm.ux[pf_r - 3][pf_c - 4] = pf_ux;
+                sm.uy[pf_r - 3][pf_c - 4] = pf_uy;
+                sm.T[pf_r - 3][pf_c - 4] = pf_T;
+                if constexpr (sizeof(real) == 4) sm.eng[pf_r - 3][pf_c - 4] = pf_E;
+            }
+        }
+        for (int e = tid + NT; e < HY * (HX - 2); e += NT) {
             const int r = e / (HX - 2), c = e - r * (HX - 2) + 1;
             const int gx = x0 - 4 + c, gyr = y0 - 3 + r;
             if (g.walls && (gx < 0 || gx >= g.nx)) continue;

@@ -1,8 +1,8 @@
 // olb_kernels.cuh -- device building blocks shared by the stage kernel
-// (olb_fused.cuh): stencil coefficients, WENO-5, equilibrium factors, Kahan
-// sums, and the initialisation / moment-output / conversion kernels,
-// templated on the population precision (double, or float with
-// Kahan-compensated moments).
+// (olb_fused.cuh): stencil coefficients, WENO-5, equilibrium factors,
+// double-float arithmetic, and the initialisation / moment-output /
+// conversion / global-sum kernels, templated on the population precision
+// (double, or float stored as hi + lo pairs).
 #pragma once
 
 #include "olb_internal.cuh"
@@ -247,19 +247,6 @@ __device__ __forceinline__ void eq_factors_split(const Tab<float> &t, float u, f
     }
 }
 
-// Kahan-compensated accumulation (FP32 variant).
-struct Kahan {
-    float s, c;
-    __device__ __forceinline__ void add(float x)
-    {
-        const float y = x - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-
 // ---------------------------------------------------------------- double-float
 // A value held as the unevaluated sum hi + lo of two floats (~44 significant
 // bits), built from error-free transformations: Knuth's TwoSum (a + b = s + e
@@ -281,7 +268,6 @@ __device__ __forceinline__ f2 fast_two_sum(float a, float b)
     const float s = a + b;
     return {s, b - (s - a)};
 }
-__device__ __forceinline__ f2 f2_from_kahan(const Kahan &k) { return fast_two_sum(k.s, -k.c); }
 __device__ __forceinline__ f2 f2_add(f2 a, f2 b)
 {
     // both parts summed exactly, then renormalised (accurate under cancellation)

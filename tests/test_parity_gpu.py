@@ -331,7 +331,7 @@ def test_phase_separation_4096_sampled_windows(olb):
     assert worst < 1.0, "; ".join(fmt_detail(d) for d in details if d["ratio"] > 0.3)
 
 
-# ------------------------------------------------------------------ FP32 + Kahan
+# ------------------------------------------------------------------ FP32 (compensated storage)
 
 def test_fp32_kahan_shear_wave(olb):
     """Shear-wave workload (64 x 4, 200 steps) in FP32: n, u, T against the
@@ -400,7 +400,7 @@ def test_every_tile_shape_gives_identical_results(olb, side_x):
 
 @pytest.mark.parametrize("side_x", [0, 1])
 def test_every_tile_shape_gives_identical_results_fp32(olb, side_x):
-    """FP32 + Kahan: the small tiles compute their faces in strips that carry
+    """FP32: the small tiles compute their faces in strips that carry
     differences and squares from face to face, the large tiles one face at a
     time; the arithmetic is the same, so every shape agrees bit for bit."""
     p = inputs.RunParams(nx=45, ny=19, ds=1.0 / 45, dt=0.2 / 45 / inputs.P_MAX, tau=0.01,

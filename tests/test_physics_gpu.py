@@ -217,8 +217,8 @@ def test_moving_bubble_is_galilean_invariant(olb):
     """Sec. 6.3: the gas bubble of radius 0.25 carried along y at u_y = V
     between a specular side (x = 0) and a diffuse wall moving at u_w = V
     (x = 1/2), periodic y, T_w = 0.8, sigma = 1e-4, ds = 1/320, dt = 2e-4;
-    V = 0, 0.01, 0.02, 0.05, 0.1 advanced together as one batch (FP32 +
-    Kahan variant).  Over 20 <= t <= 30 the Laplace-law surface tension
+    V = 0, 0.01, 0.02, 0.05, 0.1 advanced together as one batch (FP32
+    variant).  Over 20 <= t <= 30 the Laplace-law surface tension
     gamma = R_f (p^w_in - p^w_out) differs from the resting bubble's by well
     below 1 % (the paper reports under 1 %; measured <= 1.2e-3), and the
     bubble centre trails the advected position V t only slightly (the paper:
