@@ -217,9 +217,9 @@ int olb_profile(olb_ctx *ctx, int nsteps, double *ms, int *launches);
 /* Shape of the stage kernel: tx x ty nodes per CTA, kp velocities advanced
  * at once (kp lanes of tx*ty threads, each rounded up to whole warps).
  * Compiled shapes (tx, ty, kp): (8,8,4), (16,8,2), (16,8,1), (32,8,1),
- * (32,16,1), (8,8,8), (7,8,8); olb_create picks one from the
+ * (32,16,1), (8,8,8), (7,8,8), (8,8,5); olb_create picks one from the
  * grid size (FP64: (8,8,4), or (7,8,8) when that lowers the most nodes one
- * SM advances; FP32: (8,8,8), or (8,8,4) with learned weights).  With
+ * SM advances; FP32: (8,8,5), or (8,8,4) with learned weights).  With
  * OLB_WENO_LEARNED only (8,8,4), (16,8,2), (32,16,1).  olb_set_tile returns
  * OLB_ERR_ARG for any other shape; results do not depend on the shape.
  * Not part of the paper (a tuning knob). */

@@ -383,7 +383,7 @@ static void default_tile(olb_ctx *c)
         return (long long)((c->geo.nx + TILE_X[k] - 1) / TILE_X[k]) * ((c->geo.ny + TILE_Y[k] - 1) / TILE_Y[k]);
     };
     auto most_nodes = [&](int k) { return (tiles(k) + sms - 1) / sms * TILE_X[k] * TILE_Y[k]; };
-    int k = fp64 || learned ? 0 : 5;
+    int k = fp64 || learned ? 0 : 7;
     if (fp64 && !learned && most_nodes(narrow) < most_nodes(0)) k = narrow;
     c->tx = TILE_X[k];
     c->ty = TILE_Y[k];

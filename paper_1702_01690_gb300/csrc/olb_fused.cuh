@@ -802,16 +802,17 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 eq_correction(t, E, gy, sm.n[ty + 3][tx + 4], sm.eng[ty][tx], sm.ux[ty][tx], sm.uy[ty][tx], qa, qb, qc);
         }
     } else {
-        static_assert(KP == 2 || KP == 4 || KP == 8, "velocity lanes: 1, 2, 4 or 8");
+        static_assert(KP == 2 || KP == 4 || KP == 5 || KP == 8, "velocity lanes: 1, 2, 4, 5 or 8");
         using Sm = FusedSmem<real, TX, TY, KP>;
         if (active) {
             // KP = 8: lanes 0..5 take ddx, ddy, ldx, ldy, E, g(u_y);
+            // KP = 5: lanes 0..3 ddx, ddy, ldx, ldy, lane 4 E and g(u_y);
             // KP = 4: lane 0 ddx, lane 1 ddy, lane 2 ldx + E, lane 3 ldy + g(u_y);
             // KP = 2: lane 0 the x parts, lane 1 the y parts
             const bool lane_ldx = KP == 2 ? lane_k == 0 : lane_k == 2;
             const bool lane_ldy = KP == 2 ? lane_k == 1 : lane_k == 3;
             const bool lane_gx = KP == 2 ? lane_k == 0 : (KP == 4 ? lane_k == 2 : lane_k == 4);
-            const bool lane_gy = KP == 2 ? lane_k == 1 : (KP == 4 ? lane_k == 3 : lane_k == 5);
+            const bool lane_gy = KP == 2 ? lane_k == 1 : (KP == 4 ? lane_k == 3 : (KP == 5 ? lane_k == 4 : lane_k == 5));
             if (lane_k == 0) {
                 sm.loc[Sm::L_DDX][node] = grad_sum(true);
                 sm.loc[Sm::L_DN][node] = real(g.inv_ds) / field_val(sm.n[ty + cy][tx + cx]);
@@ -837,7 +838,7 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             }
             if constexpr (F32) {
                 // the equilibrium's mass and energy correction, on a lane with
-                // little else to do (KP = 8: lane 6; KP = 4, 2: lane 1), from
+                // little else to do (KP = 8: lane 6; KP = 5, 4, 2: lane 1), from
                 // the same factors the other lanes store (same operations)
                 if (lane_k == (KP == 8 ? 6 : 1)) {
                     real ex[NQ], ox[NQ], ey[NQ], oy[NQ];
@@ -960,9 +961,9 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
     // node update of velocity k (faces in slot) at tile node (tx_, ty_):
     // FP64 with Ek = E_q(k1), gyk = g_q(k2); FP32 with Ek = n ge(k1),
     // oxk = n go(k1), gyk = ge(k2), oyk = go(k2)
-    auto update = [&](int k, int slot, int tx_, int ty_, real Gx_, real Gy_, real Ek, real gyk, real oxk, real oyk,
-                      real qa_, real qb_, real qc_) {
-        const int k1 = k / NQ, k2 = k - NQ * (k / NQ);
+    auto update = [&](int k1, int k2, int slot, int tx_, int ty_, real Gx_, real Gy_, real Ek, real gyk, real oxk,
+                      real oyk, real qa_, real qb_, real qc_) {
+        const int k = NQ * k1 + k2;
         const int r = ty_ + 3, c = tx_ + 4;
         real dx = 0, dy = 0;
 #pragma unroll
@@ -1141,7 +1142,22 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             }
         }
         __syncthreads();
-        if constexpr (Sf::ALL_FACES) {
+        if constexpr (Sf::ALL_FACES && F32 && KP == NQ) {
+            // FP32 (issue-bound) node updates with five lanes: thread (node,
+            // lane k2) advances the five velocities 5 k1 + k2, k1 unrolled,
+            // so that the k1 tables are immediate operands and the node's
+            // factors are read once
+            if (active) {
+                const int k2 = lane_k;
+                const real Gx_ = sm.loc[Sf::L_G][node], Gy_ = sm.loc[Sf::L_G + 1][node];
+                const real qa_ = sm.loc[Sf::L_CA][node], qb_ = sm.loc[Sf::L_CB][node], qc_ = sm.loc[Sf::L_CC][node];
+                const real gyk = sm.loc[Sf::L_GY + k2][node], oyk = sm.loc[Sf::L_OY + k2][node];
+#pragma unroll
+                for (int k1 = 0; k1 < NQ; ++k1)
+                    update(k1, k2, NQ * k1 + k2, tx, ty, Gx_, Gy_, sm.loc[Sf::L_E + k1][node], gyk,
+                           sm.loc[Sf::L_OX + k1][node], oyk, qa_, qb_, qc_);
+            }
+        } else if constexpr (Sf::ALL_FACES) {
             // node updates, enumerated densely over (velocity, tile node)
             for (int e = tid; e < NK * NN; e += NT) {
                 const int k = e / NN, nd = e - k * NN;
@@ -1156,7 +1172,7 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                     qb_ = sm.loc[Sf::L_CB][nd];
                     qc_ = sm.loc[Sf::L_CC][nd];
                 }
-                update(k, k, tx_, ty_, sm.loc[Sf::L_G][nd], sm.loc[Sf::L_G + 1][nd], sm.loc[Sf::L_E + k1][nd],
+                update(k1, k2, k, tx_, ty_, sm.loc[Sf::L_G][nd], sm.loc[Sf::L_G + 1][nd], sm.loc[Sf::L_E + k1][nd],
                        sm.loc[Sf::L_GY + k2][nd], oxk, oyk, qa_, qb_, qc_);
             }
         } else {
@@ -1182,7 +1198,7 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                         oyk = sel5(Oy, k2);
                     }
                 }
-                update(k, lane_k, tx, ty, Gx, Gy, Ek, gyk, oxk, oyk, qa_, qb_, qc_);
+                update(k1, k2, lane_k, tx, ty, Gx, Gy, Ek, gyk, oxk, oyk, qa_, qb_, qc_);
             }
         }
     }
@@ -1420,7 +1436,7 @@ cudaError_t fused_batch_launch_one(const real *fs, const real *fn, real *out, in
 // olb_internal.cuh.
 #define OLB_FUSED_SHAPE_CASES(real, DO) \
     DO(real, 8, 8, 4) DO(real, 16, 8, 2) DO(real, 16, 8, 1) DO(real, 32, 8, 1) DO(real, 32, 16, 1) DO(real, 8, 8, 8) \
-    DO(real, 7, 8, 8)
+    DO(real, 7, 8, 8) DO(real, 8, 8, 5)
 // Shapes with a learned-weights instance (the default shapes of both precisions).
 #define OLB_FUSED_LEARNED_CASES(real, DO) DO(real, 8, 8, 4) DO(real, 16, 8, 2) DO(real, 32, 16, 1)
 #define OLB_FUSED_PREP_CASE(real, A, B, C) \

@@ -133,9 +133,9 @@ constexpr int TOTALS_BLOCKS = 1024, TOTALS_THREADS = 256;
 
 // Stage-kernel shapes compiled for both precisions: TX x TY nodes per CTA
 // and KP velocities advanced at once.
-constexpr int NUM_TILES = 7;
-constexpr int TILE_X[NUM_TILES] = {8, 16, 16, 32, 32, 8, 7};
-constexpr int TILE_Y[NUM_TILES] = {8, 8, 8, 8, 16, 8, 8};
-constexpr int TILE_K[NUM_TILES] = {4, 2, 1, 1, 1, 8, 8};
+constexpr int NUM_TILES = 8;
+constexpr int TILE_X[NUM_TILES] = {8, 16, 16, 32, 32, 8, 7, 8};
+constexpr int TILE_Y[NUM_TILES] = {8, 8, 8, 8, 16, 8, 8, 8};
+constexpr int TILE_K[NUM_TILES] = {4, 2, 1, 1, 1, 8, 8, 5};
 
 }  // namespace olb

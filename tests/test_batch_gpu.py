@@ -56,7 +56,8 @@ def test_batch_matches_single_contexts(olb, precision):
     assert rc == 0 and not per.any()
 
 
-@pytest.mark.parametrize("precision,shape", [(0, (8, 8, 4)), (0, (16, 8, 2)), (1, (8, 8, 8)), (1, (32, 16, 1))])
+@pytest.mark.parametrize("precision,shape", [(0, (8, 8, 4)), (0, (16, 8, 2)), (1, (8, 8, 8)), (1, (8, 8, 5)),
+                                             (1, (32, 16, 1))])
 def test_batch_tma_tiles_match_single_contexts(olb, precision, shape):
     """Runs large enough that most tiles lie inside their run (staged by one
     TMA copy from the run's own tensor map, the maps of the two runs side by

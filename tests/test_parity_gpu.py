@@ -376,7 +376,7 @@ def test_every_tile_shape_gives_identical_results(olb, side_x):
                          Tw=(0.85, 0.95), side_x=side_x)
     fl = noisy(p, seed=9, amp=0.05, uamp=0.01)
     ref = None
-    for shape in ((8, 8, 4), (16, 8, 2), (16, 8, 1), (32, 8, 1), (8, 8, 8), (7, 8, 8)):
+    for shape in ((8, 8, 4), (16, 8, 2), (16, 8, 1), (32, 8, 1), (8, 8, 8), (7, 8, 8), (8, 8, 5)):
         ctx = olb.create(p)
         ctx.set_tile(*shape)
         assert ctx.get_tile() == shape
@@ -407,7 +407,7 @@ def test_every_tile_shape_gives_identical_results_fp32(olb, side_x):
                          Tw=(0.85, 0.95), side_x=side_x)
     fl = noisy(p, seed=9, amp=0.05, uamp=0.01)
     ref = None
-    for shape in ((32, 16, 1), (8, 8, 4), (16, 8, 2), (16, 8, 1), (32, 8, 1), (8, 8, 8), (7, 8, 8)):
+    for shape in ((32, 16, 1), (8, 8, 4), (16, 8, 2), (16, 8, 1), (32, 8, 1), (8, 8, 8), (7, 8, 8), (8, 8, 5)):
         ctx = olb.create(p, olb.FP32_KAHAN)
         ctx.set_tile(*shape)
         ctx.init_fields(*fl)

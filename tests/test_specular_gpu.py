@@ -52,7 +52,7 @@ def test_specular_matches_oracle(olb, sides, nx, ny):
 def test_every_tile_shape_identical_with_specular_sides(olb):
     p, fl = setup(45, 19, 3, 2)
     ref = None
-    for shape in ((8, 8, 4), (16, 8, 2), (16, 8, 1), (32, 8, 1), (32, 16, 1), (8, 8, 8), (7, 8, 8)):
+    for shape in ((8, 8, 4), (16, 8, 2), (16, 8, 1), (32, 8, 1), (32, 16, 1), (8, 8, 8), (7, 8, 8), (8, 8, 5)):
         ctx = olb.create(p)
         ctx.set_tile(*shape)
         ctx.init_fields(*fl)
