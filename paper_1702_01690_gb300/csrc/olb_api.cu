@@ -7,6 +7,8 @@
 
 #include <cuda.h>
 #include <mutex>
+#include <thread>
+#include <vector>
 
 #include "../../include/olb.h"
 #include "olb_internal.cuh"
@@ -497,16 +499,55 @@ static int init_from_device(olb_ctx *c, const double *n, const double *ux, const
 }
 
 // Host fields admissible as an initial state: n > 0, b n < 1, T > 0, all
-// finite (NaN fails every comparison).  One pass without early exits.
-static bool fields_admissible(const double *n, const double *ux, const double *uy, const double *T, size_t N,
-                              double b)
+// finite (NaN fails every comparison).  One pass without early exits over
+// [q0, q1).
+static bool admissible_range(const double *n, const double *ux, const double *uy, const double *T, size_t q0,
+                             size_t q1, double b)
 {
     const double inf = HUGE_VAL;
     int ok = 1;
-    for (size_t q = 0; q < N; ++q)
+    for (size_t q = q0; q < q1; ++q)
         ok &= (n[q] > 0.0) & (n[q] < inf) & (b * n[q] < 1.0) & (T[q] > 0.0) & (T[q] < inf) & (ux[q] > -inf) &
               (ux[q] < inf) & (uy[q] > -inf) & (uy[q] < inf);
     return ok != 0;
+}
+
+// The check is bound by host memory bandwidth (32 B per node): grids of more
+// than 2^19 nodes are split over up to 16 host threads, at least 2^18 nodes
+// each (a 4096^2 grid reads 537 MB).
+bool olb::fields_admissible(const double *n, const double *ux, const double *uy, const double *T, size_t N,
+                            double b)
+{
+    constexpr size_t CHUNK = size_t(1) << 18;
+    const unsigned hw = std::thread::hardware_concurrency();
+    size_t nt = (N + CHUNK - 1) / CHUNK;
+    if (nt > 16) nt = 16;
+    if (hw > 0 && nt > hw) nt = hw;
+    if (N <= 2 * CHUNK || nt < 2) return admissible_range(n, ux, uy, T, 0, N, b);
+    std::vector<char> ok(nt, 0);
+    std::vector<std::thread> th;
+    th.reserve(nt - 1);
+    const size_t per = (N + nt - 1) / nt;
+    try {
+        for (size_t k = 1; k < nt; ++k) {
+            const size_t q0 = k * per, q1 = q0 + per < N ? q0 + per : N;
+            th.emplace_back([=, &ok] { ok[k] = admissible_range(n, ux, uy, T, q0, q1, b); });
+        }
+    } catch (...) {
+        // no thread could be started: check the rest here
+        for (auto &t : th) t.join();
+        bool all = admissible_range(n, ux, uy, T, 0, per, b);
+        for (size_t k = 1; k < nt; ++k) {
+            const size_t q0 = k * per, q1 = q0 + per < N ? q0 + per : N;
+            all = all && (k <= th.size() ? ok[k] != 0 : admissible_range(n, ux, uy, T, q0, q1, b));
+        }
+        return all;
+    }
+    ok[0] = admissible_range(n, ux, uy, T, 0, per, b);
+    for (auto &t : th) t.join();
+    for (size_t k = 0; k < nt; ++k)
+        if (!ok[k]) return false;
+    return true;
 }
 
 // Device address of page-locked (pinned, mapped) host memory, which kernels

@@ -309,12 +309,7 @@ extern "C" int olb_batch_init_fields(olb_batch *b, int run, const double *n, con
     if (!b || run < 0 || run >= b->count || !n || !ux || !uy || !T) return OLB_ERR_ARG;
     const Geo g = run_geo_at(b, run);
     const size_t N = (size_t)g.nx * g.ny;
-    const double bb = b->p[run].b;
-    for (size_t q = 0; q < N; ++q) {
-        if (!std::isfinite(n[q]) || !std::isfinite(ux[q]) || !std::isfinite(uy[q]) || !std::isfinite(T[q]))
-            return OLB_ERR_ARG;
-        if (!(n[q] > 0.0) || !(T[q] > 0.0) || !(bb * n[q] < 1.0)) return OLB_ERR_ARG;
-    }
+    if (!fields_admissible(n, ux, uy, T, N, b->p[run].b)) return OLB_ERR_ARG;
     BDevice dg(b->device);
     const double *src[4] = {n, ux, uy, T};
     cudaError_t e = cudaSuccess;

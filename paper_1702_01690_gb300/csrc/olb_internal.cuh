@@ -69,6 +69,9 @@ void fill_tab(Tab<real> *tab, const HostTables &h, const double Tw[2], const dou
 // Parameter validation of olb_create (OLB_OK / OLB_ERR_ARG / OLB_ERR_CFL)
 // and the mapping of CUDA errors to status codes (olb_api.cu).
 int validate_params(const ::olb_params *p);
+// Host fields [N] admissible as an initial state: n > 0, b n < 1, T > 0, all
+// finite (olb_api.cu; large arrays are checked by several host threads).
+bool fields_admissible(const double *n, const double *ux, const double *uy, const double *T, size_t N, double b);
 void set_sides(Geo *g, const ::olb_params *p);
 int cuda_status(cudaError_t e);
 

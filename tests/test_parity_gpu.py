@@ -237,6 +237,32 @@ def test_init_fields_rejects_invalid_values(olb):
         ctx.step(1)  # not initialised
 
 
+def test_init_fields_rejects_invalid_values_on_large_grids(olb):
+    """Grids above 2^19 nodes are checked by several host threads: one bad
+    value in any part of any field is still rejected, pinned host arrays
+    included, and a valid state is accepted afterwards."""
+    import torch
+    N = 1024
+    ds = 1.0 / N
+    p = inputs.RunParams(nx=N, ny=N, ds=ds, dt=inputs.stable_dt(ds), tau=0.01)
+    fl = inputs.shear_wave(N, N, ds, 1.0, 1.0, 1e-3)
+    ctx = olb.create(p)
+    for which, (j, i), bad in ((0, (0, 0), -1.0), (3, (N - 1, N - 1), 0.0), (1, (N // 2, 7), np.nan),
+                               (2, (700, 1000), np.inf), (0, (300, 300), 3.5)):
+        arrs = [a.copy() for a in fl]
+        arrs[which][j, i] = bad
+        with pytest.raises(olb.OlbError):
+            ctx.init_fields(*arrs)
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in fl]
+    pinned[3][N - 1, 0] = -0.5
+    with pytest.raises(olb.OlbError):
+        ctx.init_fields(*[t.numpy() for t in pinned])
+    pinned[3][N - 1, 0] = 1.0
+    ctx.init_fields(*[t.numpy() for t in pinned])
+    assert ctx.step(1) == 0
+    ctx.close()
+
+
 # ------------------------------------------------------------------ full-size samples
 
 def crop_window(fields, x0, y0, wx, wy, nx, ny, periodic_x):
