@@ -71,12 +71,37 @@ __device__ __forceinline__ void mlp_weights(const float *__restrict__ th, const 
     w[2] = e2 * inv;
 }
 
+// The network's correction sum_q w_q G_q (the interface value minus v2) of a
+// stencil that the guard hands to the network, from its first differences in
+// FP32: the normalised stencil x = (v - mean) / (max - min) taken relative to
+// v0 (shift invariant), the weights, and the candidates relative to v2.  All
+// of it runs on the FP32 pipe, in the network's precision.
+__device__ __forceinline__ float learned_corr_net(const float *__restrict__ th, float d01, float d12, float d23,
+                                                 float d34)
+{
+    const float w1 = d01, w2 = w1 + d12, w3 = w2 + d23, w4 = w3 + d34;
+    const float mx = fmaxf(fmaxf(0.0f, w1), fmaxf(fmaxf(w2, w3), w4));
+    const float mn = fminf(fminf(0.0f, w1), fminf(fminf(w2, w3), w4));
+    const float mean = (((w1 + w2) + w3) + w4) * 0.2f;
+    const float ir = 1.0f / (mx - mn);
+    const float x[MLP_IN] = {(0.0f - mean) * ir, (w1 - mean) * ir, (w2 - mean) * ir, (w3 - mean) * ir,
+                             (w4 - mean) * ir};
+    float w[MLP_OUT];
+    mlp_weights(th, x, w);
+    const float G1 = fmaf(5.0f / 6.0f, d12, (-1.0f / 3.0f) * d01);
+    const float G2 = fmaf(1.0f / 3.0f, d23, (1.0f / 6.0f) * d12);
+    const float G3 = fmaf(2.0f / 3.0f, d23, (-1.0f / 6.0f) * d34);
+    return fmaf(w[0], G1, fmaf(w[1], G2, w[2] * G3));
+}
+
 // Learned WENO-5 interface value (without p/m) of the upwind-ordered stencil:
 // where any smoothness indicator vanishes the Jiang-Shu weights with Table
 // tab:weno apply (constant ghost layers keep their exact flux), and so do
 // they where the stencil is smooth (min sigma_q >= MLP_GUARD max sigma_q);
-// otherwise v2 + sum_q w_q G_q with the network's weights.  The network runs
-// in FP32; the candidates are combined in the population precision.
+// otherwise v2 + sum_q w_q G_q with the network's weights.  The guard is
+// taken in the population precision; the network and the correction
+// sum_q w_q G_q run in FP32 (the weights carry FP32 error anyway), and the
+// correction is added to v2 in the population precision.
 template <typename real>
 __device__ __forceinline__ real weno5_learned(const float *__restrict__ th, real v0, real v1, real v2, real v3,
                                               real v4)
@@ -88,30 +113,31 @@ __device__ __forceinline__ real weno5_learned(const float *__restrict__ th, real
     const real s1 = fma(real(13) * a1, a1, real(3) * b1 * b1);
     const real s2 = fma(real(13) * a2, a2, real(3) * b2 * b2);
     const real s3 = fma(real(13) * a3, a3, real(3) * b3 * b3);
-    const real smin = s1 < s2 ? (s1 < s3 ? s1 : s3) : (s2 < s3 ? s2 : s3);
-    const real smax = s1 > s2 ? (s1 > s3 ? s1 : s3) : (s2 > s3 ? s2 : s3);
-    const bool zero = (a1 == real(0) && b1 == real(0)) || (a2 == real(0) && b2 == real(0)) ||
-                      (a3 == real(0) && b3 == real(0));
-    if (zero || smin >= real(MLP_GUARD) * smax) return weno5(v0, v1, v2, v3, v4);
-    real mx = v0, mn = v0;
-    mx = v1 > mx ? v1 : mx;
-    mn = v1 < mn ? v1 : mn;
-    mx = v2 > mx ? v2 : mx;
-    mn = v2 < mn ? v2 : mn;
-    mx = v3 > mx ? v3 : mx;
-    mn = v3 < mn ? v3 : mn;
-    mx = v4 > mx ? v4 : mx;
-    mn = v4 < mn ? v4 : mn;
-    const real mean = (v0 + v1 + v2 + v3 + v4) * real(0.2);
-    const real ir = real(1) / (mx - mn);
-    const float x[MLP_IN] = {(float)((v0 - mean) * ir), (float)((v1 - mean) * ir), (float)((v2 - mean) * ir),
-                             (float)((v3 - mean) * ir), (float)((v4 - mean) * ir)};
-    float w[MLP_OUT];
-    mlp_weights(th, x, w);
-    const real G1 = fma(real(5.0 / 6.0), d12, real(-1.0 / 3.0) * d01);
-    const real G2 = fma(real(1.0 / 3.0), d23, real(1.0 / 6.0) * d12);
-    const real G3 = fma(real(2.0 / 3.0), d23, real(-1.0 / 6.0) * d34);
-    return fma((real)w[0], G1, fma((real)w[1], G2, fma((real)w[2], G3, v2)));
+    real smin, smax;
+    bool zero;
+    if constexpr (sizeof(real) == 8) {
+        // on the integer pipe (the FP64 pipe bounds this kernel): the
+        // indicators are >= 0, whose bit patterns order like their values,
+        // and x == 0 (either sign) is a zero pattern without the sign bit
+        const long long i1 = __double_as_longlong(s1), i2 = __double_as_longlong(s2), i3 = __double_as_longlong(s3);
+        smin = i1 < i2 ? (i1 < i3 ? s1 : s3) : (i2 < i3 ? s2 : s3);
+        smax = i1 > i2 ? (i1 > i3 ? s1 : s3) : (i2 > i3 ? s2 : s3);
+        auto z = [](real v) { return (__double_as_longlong(v) << 1) == 0; };
+        zero = (z(a1) && z(b1)) || (z(a2) && z(b2)) || (z(a3) && z(b3));
+    } else {
+        smin = s1 < s2 ? (s1 < s3 ? s1 : s3) : (s2 < s3 ? s2 : s3);
+        smax = s1 > s2 ? (s1 > s3 ? s1 : s3) : (s2 > s3 ? s2 : s3);
+        zero = (a1 == real(0) && b1 == real(0)) || (a2 == real(0) && b2 == real(0)) ||
+               (a3 == real(0) && b3 == real(0));
+    }
+    if (zero || smin >= real(MLP_GUARD) * smax) {
+        // Jiang-Shu on the same differences (the operations of weno5)
+        const real q12 = d12 * d12, q23 = d23 * d23;
+        return weno5_core(d01, d12, d23, d34, q23, real(2.5) * q12, real(2.5) * q23, v2);
+    }
+    // the guard above is taken in the population precision; the network's
+    // input and correction in its own (FP32)
+    return v2 + (real)learned_corr_net(th, (float)d01, (float)d12, (float)d23, (float)d34);
 }
 
 // The same for the compensated FP32 storage: the correction sum_q w_q G_q (the
@@ -129,20 +155,7 @@ __device__ __forceinline__ float weno5_learned_corr(const float *__restrict__ th
     const float smin = fminf(s1, fminf(s2, s3)), smax = fmaxf(s1, fmaxf(s2, s3));
     const bool zero = (a1 == 0.0f && b1 == 0.0f) || (a2 == 0.0f && b2 == 0.0f) || (a3 == 0.0f && b3 == 0.0f);
     if (zero || smin >= (float)MLP_GUARD * smax) return weno5_corr(d01, d12, d23, d34);
-    // the stencil relative to v0
-    const float w1 = d01, w2 = w1 + d12, w3 = w2 + d23, w4 = w3 + d34;
-    const float mx = fmaxf(fmaxf(0.0f, w1), fmaxf(fmaxf(w2, w3), w4));
-    const float mn = fminf(fminf(0.0f, w1), fminf(fminf(w2, w3), w4));
-    const float mean = (((w1 + w2) + w3) + w4) * 0.2f;
-    const float ir = 1.0f / (mx - mn);
-    const float x[MLP_IN] = {(0.0f - mean) * ir, (w1 - mean) * ir, (w2 - mean) * ir, (w3 - mean) * ir,
-                             (w4 - mean) * ir};
-    float w[MLP_OUT];
-    mlp_weights(th, x, w);
-    const float G1 = fmaf(5.0f / 6.0f, d12, (-1.0f / 3.0f) * d01);
-    const float G2 = fmaf(1.0f / 3.0f, d23, (1.0f / 6.0f) * d12);
-    const float G3 = fmaf(2.0f / 3.0f, d23, (-1.0f / 6.0f) * d34);
-    return fmaf(w[0], G1, fmaf(w[1], G2, w[2] * G3));
+    return learned_corr_net(th, d01, d12, d23, d34);
 }
 
 // ---------------------------------------------------------------- the network on the tensor pipe
