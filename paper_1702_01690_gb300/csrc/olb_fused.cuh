@@ -1030,27 +1030,52 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             // evaluate it per thread in the loop further down: that measured
             // faster there).  The faces of this pass (all 25 velocities' on small tiles, else
             // those of velocities kb .. kb+KP-1), enumerated as below, on
-            // whole warps: items past the end take part in the network only
+            // whole warps: items past the end take part in the network only.
+            // Small tiles: the x faces of the 20 velocities with xi_x != 0,
+            // then the y faces of the 20 with xi_y != 0, located by division
+            // (as in the dense pass below); otherwise the KP velocities'
+            // faces, located in their prefix table
             int end[KF], total = 0;
+            if constexpr (Sf::ALL_FACES) {
+                total = 20 * (nfx + nfy);
+            } else {
 #pragma unroll
-            for (int sub = 0; sub < KF; ++sub) {
-                const int k = kb + sub;
-                if (k < NK) total += (k / NQ != 2 ? nfx : 0) + (k % NQ != 2 ? nfy : 0);
-                end[sub] = total;
+                for (int sub = 0; sub < KF; ++sub) {
+                    const int k = kb + sub;
+                    if (k < NK) total += (k / NQ != 2 ? nfx : 0) + (k % NQ != 2 ? nfy : 0);
+                    end[sub] = total;
+                }
             }
             const int padded = (total + 31) & ~31;
             for (int e = tid; e < padded; e += NT) {
-                int sub = 0, start = 0;
-#pragma unroll
-                for (int q = 0; q + 1 < KF; ++q)
-                    if (e >= end[q]) {
-                        sub = q + 1;
-                        start = end[q];
+                int k, sub, f;
+                bool valid = e < total;
+                if constexpr (Sf::ALL_FACES) {
+                    const int ee = valid ? e : 0;
+                    if (ee < 20 * nfx) {
+                        const int kx = ee / nfx;
+                        k = kx < 2 * NQ ? kx : kx + NQ;
+                        f = ee - kx * nfx;
+                    } else {
+                        const int e2 = ee - 20 * nfx, ky = e2 / nfy, q = ky & 3;
+                        k = (ky >> 2) * NQ + (q < 2 ? q : q + 1);
+                        f = nfx + e2 - ky * nfy;
                     }
-                const int k = kb + sub;
-                int f = e - start;
-                if (k / NQ == 2) f += nfx;
-                const bool valid = e < total && k < NK;
+                    sub = k;
+                } else {
+                    int start = 0;
+                    sub = 0;
+#pragma unroll
+                    for (int q = 0; q + 1 < KF; ++q)
+                        if (e >= end[q]) {
+                            sub = q + 1;
+                            start = end[q];
+                        }
+                    k = kb + sub;
+                    f = e - start;
+                    if (k / NQ == 2) f += nfx;
+                    valid = valid && k < NK;
+                }
                 const bool along_x = f < nfx;
                 const int r = along_x ? f / (TX + 1) : (f - nfx) / TX;
                 const int c = along_x ? f - r * (TX + 1) : f - nfx - r * TX;
