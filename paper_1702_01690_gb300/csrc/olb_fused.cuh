@@ -942,14 +942,18 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
                 v2 = P[at(2)];
             }
         }
+        // the guard in the population precision, the network's input and
+        // correction in FP32 from the rounded differences
+        const bool acts = learned_guard<real>(d[0], d[1], d[2], d[3]);
+        const float e[4] = {(float)d[0], (float)d[1], (float)d[2], (float)d[3]};
         float x[MLP_IN], w[MLP_OUT] = {0.0f, 0.0f, 0.0f};
-        const bool acts = learned_input<real>(d[0], d[1], d[2], d[3], x);
+        learned_input_x(e, acts, x);
         // the whole warp skips the network when none of its stencils needs it
         if (__any_sync(0xffffffffu, acts)) mlp_weights_warp(mlp, x, w, mlp_sc);
         if (valid) {
             real res;
             if (acts) {
-                res = learned_combine<real>(w, d[0], d[1], d[2], d[3], v2);
+                res = v2 + (real)learned_corr_from(w, e);
             } else {
                 const real q12 = d[1] * d[1], q23 = d[2] * d[2];
                 res = weno5_core(d[0], d[1], d[2], d[3], q23, real(2.5) * q12, real(2.5) * q23, v2);
@@ -1027,8 +1031,9 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
         if constexpr (LEARNED && sizeof(real) == 4) {
             // FP32 with learned weights: the network on the tensor pipe, one
             // warp per 32 stencils (FP64 instances, bound by the FP64 pipe,
-            // evaluate it per thread in the loop further down: that measured
-            // faster there).  The faces of this pass (all 25 velocities' on small tiles, else
+            // evaluate it per thread in the loop further down: the warp
+            // network measured no faster there, and its scratch does not fit
+            // the largest FP64 tile).  The faces of this pass (all 25 velocities' on small tiles, else
             // those of velocities kb .. kb+KP-1), enumerated as below, on
             // whole warps: items past the end take part in the network only.
             // Small tiles: the x faces of the 20 velocities with xi_x != 0,

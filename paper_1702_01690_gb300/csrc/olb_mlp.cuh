@@ -71,27 +71,72 @@ __device__ __forceinline__ void mlp_weights(const float *__restrict__ th, const 
     w[2] = e2 * inv;
 }
 
-// The network's correction sum_q w_q G_q (the interface value minus v2) of a
-// stencil that the guard hands to the network, from its first differences in
-// FP32: the normalised stencil x = (v - mean) / (max - min) taken relative to
-// v0 (shift invariant), the weights, and the candidates relative to v2.  All
-// of it runs on the FP32 pipe, in the network's precision.
-__device__ __forceinline__ float learned_corr_net(const float *__restrict__ th, float d01, float d12, float d23,
-                                                 float d34)
+// Whether the network acts on the stencil with first differences d01 .. d34:
+// no smoothness indicator vanishes and min sigma_q < MLP_GUARD max sigma_q
+// (otherwise Jiang-Shu with Table tab:weno applies).  Taken in the
+// population precision; FP64 compares on the integer pipe (the FP64 pipe
+// bounds that kernel): the indicators are >= 0, whose bit patterns order like
+// their values, and x == 0 (either sign) is a zero pattern without the sign bit.
+template <typename real>
+__device__ __forceinline__ bool learned_guard(real d01, real d12, real d23, real d34)
 {
-    const float w1 = d01, w2 = w1 + d12, w3 = w2 + d23, w4 = w3 + d34;
+    const real a1 = d12 - d01, b1 = fma(real(3), d12, -d01);
+    const real a2 = d23 - d12, b2 = d12 + d23;
+    const real a3 = d34 - d23, b3 = fma(real(-3), d23, d34);
+    const real s1 = fma(real(13) * a1, a1, real(3) * b1 * b1);
+    const real s2 = fma(real(13) * a2, a2, real(3) * b2 * b2);
+    const real s3 = fma(real(13) * a3, a3, real(3) * b3 * b3);
+    real smin, smax;
+    bool zero;
+    if constexpr (sizeof(real) == 8) {
+        const long long i1 = __double_as_longlong(s1), i2 = __double_as_longlong(s2), i3 = __double_as_longlong(s3);
+        smin = i1 < i2 ? (i1 < i3 ? s1 : s3) : (i2 < i3 ? s2 : s3);
+        smax = i1 > i2 ? (i1 > i3 ? s1 : s3) : (i2 > i3 ? s2 : s3);
+        auto z = [](real v) { return (__double_as_longlong(v) << 1) == 0; };
+        zero = (z(a1) && z(b1)) || (z(a2) && z(b2)) || (z(a3) && z(b3));
+    } else {
+        smin = fminf(s1, fminf(s2, s3));
+        smax = fmaxf(s1, fmaxf(s2, s3));
+        zero = (a1 == 0.0f && b1 == 0.0f) || (a2 == 0.0f && b2 == 0.0f) || (a3 == 0.0f && b3 == 0.0f);
+    }
+    return !zero && smin < real(MLP_GUARD) * smax;
+}
+
+// The network's input from the stencil's first differences in FP32: the
+// normalised stencil x = (v - mean) / (max - min), taken relative to v0
+// (shift invariant); all zero where the network does not act.
+__device__ __forceinline__ void learned_input_x(const float e[4], bool acts, float x[MLP_IN])
+{
+    const float w1 = e[0], w2 = w1 + e[1], w3 = w2 + e[2], w4 = w3 + e[3];
     const float mx = fmaxf(fmaxf(0.0f, w1), fmaxf(fmaxf(w2, w3), w4));
     const float mn = fminf(fminf(0.0f, w1), fminf(fminf(w2, w3), w4));
     const float mean = (((w1 + w2) + w3) + w4) * 0.2f;
-    const float ir = 1.0f / (mx - mn);
-    const float x[MLP_IN] = {(0.0f - mean) * ir, (w1 - mean) * ir, (w2 - mean) * ir, (w3 - mean) * ir,
-                             (w4 - mean) * ir};
-    float w[MLP_OUT];
-    mlp_weights(th, x, w);
-    const float G1 = fmaf(5.0f / 6.0f, d12, (-1.0f / 3.0f) * d01);
-    const float G2 = fmaf(1.0f / 3.0f, d23, (1.0f / 6.0f) * d12);
-    const float G3 = fmaf(2.0f / 3.0f, d23, (-1.0f / 6.0f) * d34);
+    const float ir = acts ? 1.0f / (mx - mn) : 0.0f;
+    x[0] = (0.0f - mean) * ir;
+    x[1] = (w1 - mean) * ir;
+    x[2] = (w2 - mean) * ir;
+    x[3] = (w3 - mean) * ir;
+    x[4] = (w4 - mean) * ir;
+}
+
+// The correction sum_q w_q G_q (the interface value minus v2, Eq. weno5_flux)
+// from the network's weights and the first differences, in FP32 (the weights
+// carry FP32 error anyway).
+__device__ __forceinline__ float learned_corr_from(const float w[MLP_OUT], const float e[4])
+{
+    const float G1 = fmaf(5.0f / 6.0f, e[1], (-1.0f / 3.0f) * e[0]);
+    const float G2 = fmaf(1.0f / 3.0f, e[2], (1.0f / 6.0f) * e[1]);
+    const float G3 = fmaf(2.0f / 3.0f, e[2], (-1.0f / 6.0f) * e[3]);
     return fmaf(w[0], G1, fmaf(w[1], G2, w[2] * G3));
+}
+
+// The network's correction of a stencil it acts on (per thread).
+__device__ __forceinline__ float learned_corr_net(const float *__restrict__ th, const float e[4])
+{
+    float x[MLP_IN], w[MLP_OUT];
+    learned_input_x(e, true, x);
+    mlp_weights(th, x, w);
+    return learned_corr_from(w, e);
 }
 
 // Learned WENO-5 interface value (without p/m) of the upwind-ordered stencil:
@@ -107,37 +152,13 @@ __device__ __forceinline__ real weno5_learned(const float *__restrict__ th, real
                                               real v4)
 {
     const real d01 = v1 - v0, d12 = v2 - v1, d23 = v3 - v2, d34 = v4 - v3;
-    const real a1 = d12 - d01, b1 = fma(real(3), d12, -d01);
-    const real a2 = d23 - d12, b2 = d12 + d23;
-    const real a3 = d34 - d23, b3 = fma(real(-3), d23, d34);
-    const real s1 = fma(real(13) * a1, a1, real(3) * b1 * b1);
-    const real s2 = fma(real(13) * a2, a2, real(3) * b2 * b2);
-    const real s3 = fma(real(13) * a3, a3, real(3) * b3 * b3);
-    real smin, smax;
-    bool zero;
-    if constexpr (sizeof(real) == 8) {
-        // on the integer pipe (the FP64 pipe bounds this kernel): the
-        // indicators are >= 0, whose bit patterns order like their values,
-        // and x == 0 (either sign) is a zero pattern without the sign bit
-        const long long i1 = __double_as_longlong(s1), i2 = __double_as_longlong(s2), i3 = __double_as_longlong(s3);
-        smin = i1 < i2 ? (i1 < i3 ? s1 : s3) : (i2 < i3 ? s2 : s3);
-        smax = i1 > i2 ? (i1 > i3 ? s1 : s3) : (i2 > i3 ? s2 : s3);
-        auto z = [](real v) { return (__double_as_longlong(v) << 1) == 0; };
-        zero = (z(a1) && z(b1)) || (z(a2) && z(b2)) || (z(a3) && z(b3));
-    } else {
-        smin = s1 < s2 ? (s1 < s3 ? s1 : s3) : (s2 < s3 ? s2 : s3);
-        smax = s1 > s2 ? (s1 > s3 ? s1 : s3) : (s2 > s3 ? s2 : s3);
-        zero = (a1 == real(0) && b1 == real(0)) || (a2 == real(0) && b2 == real(0)) ||
-               (a3 == real(0) && b3 == real(0));
-    }
-    if (zero || smin >= real(MLP_GUARD) * smax) {
+    if (!learned_guard<real>(d01, d12, d23, d34)) {
         // Jiang-Shu on the same differences (the operations of weno5)
         const real q12 = d12 * d12, q23 = d23 * d23;
         return weno5_core(d01, d12, d23, d34, q23, real(2.5) * q12, real(2.5) * q23, v2);
     }
-    // the guard above is taken in the population precision; the network's
-    // input and correction in its own (FP32)
-    return v2 + (real)learned_corr_net(th, (float)d01, (float)d12, (float)d23, (float)d34);
+    const float e[4] = {(float)d01, (float)d12, (float)d23, (float)d34};
+    return v2 + (real)learned_corr_net(th, e);
 }
 
 // The same for the compensated FP32 storage: the correction sum_q w_q G_q (the
@@ -146,16 +167,9 @@ __device__ __forceinline__ real weno5_learned(const float *__restrict__ th, real
 __device__ __forceinline__ float weno5_learned_corr(const float *__restrict__ th, float d01, float d12, float d23,
                                                    float d34)
 {
-    const float a1 = d12 - d01, b1 = fmaf(3.0f, d12, -d01);
-    const float a2 = d23 - d12, b2 = d12 + d23;
-    const float a3 = d34 - d23, b3 = fmaf(-3.0f, d23, d34);
-    const float s1 = fmaf(13.0f * a1, a1, 3.0f * b1 * b1);
-    const float s2 = fmaf(13.0f * a2, a2, 3.0f * b2 * b2);
-    const float s3 = fmaf(13.0f * a3, a3, 3.0f * b3 * b3);
-    const float smin = fminf(s1, fminf(s2, s3)), smax = fmaxf(s1, fmaxf(s2, s3));
-    const bool zero = (a1 == 0.0f && b1 == 0.0f) || (a2 == 0.0f && b2 == 0.0f) || (a3 == 0.0f && b3 == 0.0f);
-    if (zero || smin >= (float)MLP_GUARD * smax) return weno5_corr(d01, d12, d23, d34);
-    return learned_corr_net(th, d01, d12, d23, d34);
+    if (!learned_guard<float>(d01, d12, d23, d34)) return weno5_corr(d01, d12, d23, d34);
+    const float e[4] = {d01, d12, d23, d34};
+    return learned_corr_net(th, e);
 }
 
 // ---------------------------------------------------------------- the network on the tensor pipe
@@ -296,48 +310,6 @@ __device__ __forceinline__ void mlp_weights_warp(const float *__restrict__ th, c
     w[0] = __shfl_sync(0xffffffffu, e0 * inv, src);
     w[1] = __shfl_sync(0xffffffffu, e1 * inv, src);
     w[2] = __shfl_sync(0xffffffffu, e2 * inv, src);
-}
-
-// The learned interface value from the stencil's first differences d01 ..
-// d34 (and, in FP64, its upwind node v2): whether the network acts (no
-// vanishing indicator, min sigma_q < MLP_GUARD max sigma_q) and its
-// normalised input x (shift invariant: the stencil relative to v0).
-template <typename real>
-__device__ __forceinline__ bool learned_input(real d01, real d12, real d23, real d34, float x[MLP_IN])
-{
-    const real a1 = d12 - d01, b1 = fma(real(3), d12, -d01);
-    const real a2 = d23 - d12, b2 = d12 + d23;
-    const real a3 = d34 - d23, b3 = fma(real(-3), d23, d34);
-    const real s1 = fma(real(13) * a1, a1, real(3) * b1 * b1);
-    const real s2 = fma(real(13) * a2, a2, real(3) * b2 * b2);
-    const real s3 = fma(real(13) * a3, a3, real(3) * b3 * b3);
-    const real smin = s1 < s2 ? (s1 < s3 ? s1 : s3) : (s2 < s3 ? s2 : s3);
-    const real smax = s1 > s2 ? (s1 > s3 ? s1 : s3) : (s2 > s3 ? s2 : s3);
-    const bool zero = (a1 == real(0) && b1 == real(0)) || (a2 == real(0) && b2 == real(0)) ||
-                      (a3 == real(0) && b3 == real(0));
-    const bool acts = !zero && smin < real(MLP_GUARD) * smax;
-    const real w1 = d01, w2 = w1 + d12, w3 = w2 + d23, w4 = w3 + d34;
-    const real mx = fmax(fmax(real(0), w1), fmax(fmax(w2, w3), w4));
-    const real mn = fmin(fmin(real(0), w1), fmin(fmin(w2, w3), w4));
-    const real mean = (((w1 + w2) + w3) + w4) * real(0.2);
-    const real ir = acts ? real(1) / (mx - mn) : real(0);
-    x[0] = (float)((real(0) - mean) * ir);
-    x[1] = (float)((w1 - mean) * ir);
-    x[2] = (float)((w2 - mean) * ir);
-    x[3] = (float)((w3 - mean) * ir);
-    x[4] = (float)((w4 - mean) * ir);
-    return acts;
-}
-
-// v2 + sum_q w_q (Fhat^q - v2) (Eq. weno5_flux) from first differences.
-template <typename real>
-__device__ __forceinline__ real learned_combine(const float w[MLP_OUT], real d01, real d12, real d23, real d34,
-                                                real v2)
-{
-    const real G1 = fma(real(5.0 / 6.0), d12, real(-1.0 / 3.0) * d01);
-    const real G2 = fma(real(1.0 / 3.0), d23, real(1.0 / 6.0) * d12);
-    const real G3 = fma(real(2.0 / 3.0), d23, real(-1.0 / 6.0) * d34);
-    return fma((real)w[0], G1, fma((real)w[1], G2, fma((real)w[2], G3, v2)));
 }
 
 }  // namespace olb
