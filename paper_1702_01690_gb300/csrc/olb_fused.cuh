@@ -356,14 +356,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity)
 // Phase 1 for a tile whose staged region lies inside the grid: one TMA copy
 // of the box (HX, HY, planes) at (gx0, gy0, 0) of the tensor map into the
 // staging arrays (pop, then the lo planes in FP32, contiguous in FusedSmem in
-// the box's order), completion tracked by an mbarrier.  If the bounded wait
-// runs out, bit 1 of the status word is set, the copy is waited for once more
-// (bounded) and false is returned: the caller leaves the tile untouched and
-// the CTA stops.  After a completed copy the barrier is invalidated, so that
-// a CTA that stages several tiles initialises it afresh for each.
+// the box's order), completion tracked by an mbarrier.  tma_issue starts the
+// copy (all threads call it; it synchronises); tma_finish waits for it with
+// the bounded wait.  If the wait runs out, bit 1 of the status word is set,
+// the copy is waited for once more (bounded) and false is returned: the
+// caller leaves the tile untouched and the CTA stops.  After a completed copy
+// the barrier is invalidated, so that a CTA that stages several tiles
+// initialises it afresh for each.
 template <typename real, int TX, int TY, int KP>
-__device__ __forceinline__ bool tma_stage(FusedSmem<real, TX, TY, KP> &sm, const TmaMap *tmap, int gx0, int gy0,
-                                          int *status)
+__device__ __forceinline__ void tma_issue(FusedSmem<real, TX, TY, KP> &sm, const TmaMap *tmap, int gx0, int gy0)
 {
     constexpr unsigned bytes = sizeof(sm.pop) + (sizeof(real) == 4 ? sizeof(sm.pop) : 0);
     const unsigned mbar = (unsigned)__cvta_generic_to_shared(&sm.mbar);
@@ -380,6 +381,11 @@ __device__ __forceinline__ bool tma_stage(FusedSmem<real, TX, TY, KP> &sm, const
             : "memory");
     }
     __syncthreads();  // the barrier is initialised before anyone waits on it
+}
+template <typename real, int TX, int TY, int KP>
+__device__ __forceinline__ bool tma_finish(FusedSmem<real, TX, TY, KP> &sm, int *status)
+{
+    const unsigned mbar = (unsigned)__cvta_generic_to_shared(&sm.mbar);
     const bool ok = mbar_wait(mbar, 0);
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) atomicOr(status, 2);
@@ -456,8 +462,13 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             }
         }
     }
+    // With the moments from the pre-pass, a tile inside the grid touches its
+    // staged populations first in the face pass (no walls, no sides, no
+    // moments to compute), so phases 2-4 run while the copy is in flight
+    const bool defer = inside && fields != nullptr;
     if (inside) {
-        if (!tma_stage(sm, tmap, x0 - 4, y0 - 3, status)) return false;
+        tma_issue(sm, tmap, x0 - 4, y0 - 3);
+        if (!defer && !tma_finish(sm, status)) return false;
     } else {
         for (int e = tid; e < HY * HX; e += NT) {
             const int r = e / HX, c = e - r * HX;
@@ -1026,6 +1037,7 @@ __device__ __forceinline__ bool stage_tile(FusedSmem<real, TX, TY, KP> &sm, cons
             out[k * g.plane + o] = v;
         }
     };
+    if (defer && !tma_finish(sm, status)) return false;  // the populations of phase 1
     for (int kb = 0; kb < NK; kb += KF) {
         __syncthreads();  // loc ready / the previous velocities' faces are consumed
         if constexpr (LEARNED && sizeof(real) == 4) {
