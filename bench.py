@@ -73,9 +73,9 @@ VALUES_PER_NODE_STEP = 200
 # 4096^2 grid (traffic grows with the node count).  Any other kernel or
 # workload reports null.
 DRAM_TRAFFIC_PER_LAUNCH = {
-    # 2048^2, stages 1, 2, 3: 1.823, 2.670, 2.658 GB (FP64) and 1.817, 2.667, 2.654 GB (FP32); mean x 4
-    ("phase", None, "k_fused<double,8,8,4>"): 4 * (1.823 + 2.670 + 2.658) / 3 * 1e9,
-    ("phase", None, "k_fused<float,8,8,5>"): 4 * (1.817 + 2.667 + 2.654) / 3 * 1e9,
+    # 2048^2, stages 1, 2, 3: 1.820, 2.669, 2.658 GB (FP64) and 1.818, 2.668, 2.655 GB (FP32); mean x 4
+    ("phase", None, "k_fused<double,8,8,4>"): 4 * (1.820 + 2.669 + 2.658) / 3 * 1e9,
+    ("phase", None, "k_fused<float,8,8,5>"): 4 * (1.818 + 2.668 + 2.655) / 3 * 1e9,
 }
 
 
