@@ -80,6 +80,31 @@ __device__ __forceinline__ void mlp_weights(const float *__restrict__ th, const 
 template <typename real>
 __device__ __forceinline__ bool learned_guard(real d01, real d12, real d23, real d34)
 {
+    if constexpr (sizeof(real) == 8) {
+        // a_q = b_q = 0 exactly when both differences of sub-stencil q are 0
+        // (a difference of two numbers is 0 only when they are equal, and an
+        // FMA is exact before its one rounding)
+        auto z = [](double v) { return (__double_as_longlong(v) << 1) == 0; };
+        if ((z(d01) && z(d12)) || (z(d12) && z(d23)) || (z(d23) && z(d34))) return false;
+        // FP32 pre-check: each sigma_q is a positive-definite quadratic form in
+        // two differences (condition number ~18), so from the differences
+        // rounded to FP32 it carries a relative error below ~3e-6; outside a
+        // band of 1e-4 around the threshold the FP32 comparison is the FP64
+        // one.  Inside the band, or with squares near FP32's range limits,
+        // the FP64 test below decides.
+        const float e01 = (float)d01, e12 = (float)d12, e23 = (float)d23, e34 = (float)d34;
+        const float fa1 = e12 - e01, fb1 = fmaf(3.0f, e12, -e01);
+        const float fa2 = e23 - e12, fb2 = e12 + e23;
+        const float fa3 = e34 - e23, fb3 = fmaf(-3.0f, e23, e34);
+        const float f1 = fmaf(13.0f * fa1, fa1, 3.0f * fb1 * fb1);
+        const float f2v = fmaf(13.0f * fa2, fa2, 3.0f * fb2 * fb2);
+        const float f3 = fmaf(13.0f * fa3, fa3, 3.0f * fb3 * fb3);
+        const float fmn = fminf(f1, fminf(f2v, f3)), fmx = fmaxf(f1, fmaxf(f2v, f3));
+        if (fmx > 1e-30f && fmx < 1e30f) {
+            if (fmn < (float)(MLP_GUARD * (1.0 - 1e-4)) * fmx) return true;
+            if (fmn > (float)(MLP_GUARD * (1.0 + 1e-4)) * fmx) return false;
+        }
+    }
     const real a1 = d12 - d01, b1 = fma(real(3), d12, -d01);
     const real a2 = d23 - d12, b2 = d12 + d23;
     const real a3 = d34 - d23, b3 = fma(real(-3), d23, d34);
