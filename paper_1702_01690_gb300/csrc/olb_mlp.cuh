@@ -73,10 +73,13 @@ __device__ __forceinline__ void mlp_weights(const float *__restrict__ th, const 
 
 // Whether the network acts on the stencil with first differences d01 .. d34:
 // no smoothness indicator vanishes and min sigma_q < MLP_GUARD max sigma_q
-// (otherwise Jiang-Shu with Table tab:weno applies).  Taken in the
-// population precision; FP64 compares on the integer pipe (the FP64 pipe
-// bounds that kernel): the indicators are >= 0, whose bit patterns order like
-// their values, and x == 0 (either sign) is a zero pattern without the sign bit.
+// (otherwise Jiang-Shu with Table tab:weno applies).  The decision is that of
+// the population precision.  FP64 spares its FP64 pipe (which bounds that
+// kernel): the zero test is on the differences' bits, an FP32 pre-check
+// decides away from the threshold, and the FP64 indicators that remain are
+// compared on the integer pipe (they are >= 0, and their bit patterns order
+// like their values; x == 0 of either sign is a zero pattern without the sign
+// bit).
 template <typename real>
 __device__ __forceinline__ bool learned_guard(real d01, real d12, real d23, real d34)
 {
